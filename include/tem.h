@@ -1,0 +1,207 @@
+/*
+ * tem.h -- C ABI of the GB300 step-off TEM forward model.
+ *
+ * The method (Boerner & Guettel, "Fast parallel transient electromagnetic
+ * modeling using a uniform-in-time approximation to the exponential"):
+ * the semi-discrete step-off field u(t) = exp(-t M^{-1} K) M^{-1} f
+ * (Sec. 2.2, Eq. (expm)) is approximated at every channel t_k by one family
+ * of rational functions with shared poles (Sec. 3.2, Eq. (ratfam)), so that
+ *
+ *     d_t b_z(r, t_k) ~= sum_i Re( c[i, k] q_r^T (K - xi_i M)^{-1} f )      (Eq. (rmj), (rmjQ))
+ *
+ * with one shifted solve per conjugate pair of poles, independent of the
+ * number of channels.  K is the curl-curl operator and M the lumped
+ * conductivity mass on a staggered (Yee) edge grid; f is a closed loop of
+ * current; q_r reads d_t b_z at receiver r.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  * Units: metres, seconds, S/m, amperes; mu0 = 4 pi 1e-7.  z points up.
+ *  * Cells: nx x ny x nz with widths hx[nx], hy[ny], hz[nz] (> 0) from the
+ *    corner `origin`.  Per-cell arrays are (nz, ny, nx), x fastest.
+ *  * Complex numbers are interleaved (re, im) pairs of doubles.
+ *  * Host pointers are owned by the caller and only read (or written, for
+ *    outputs) during the call; the library keeps no reference to them.
+ *  * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Host
+ *    outputs are complete when the call returns (it synchronises the stream).
+ *  * Every entry point returns a status (TEM_OK = 0 on success) and never
+ *    aborts the process; tem_status_string() names the code.  On an error
+ *    other than TEM_ENOCONV no output is written.
+ *  * Device memory comes from cudaMallocAsync on `cuda_stream`, or from the
+ *    allocator installed with tem_set_allocator().
+ *
+ * Edge layout on the device (for tem_apply_operator): one complex vector is
+ * 3 blocks (x-, y-, z-edges) of nx*ny*nz entries each, entry (c, i, j, k) at
+ * c*nx*ny*nz + i + nx*(j + ny*k).  Entry (c, i, j, k) is the edge of
+ * direction c leaving node (i, j, k).  Edges lying in the domain boundary
+ * (n x e = 0, Eq. (bc)) hold 0; so do the padding entries (x-edges at
+ * j = 0 or k = 0, and likewise for y and z).
+ */
+#ifndef TEM_H_
+#define TEM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+  TEM_OK = 0,
+  TEM_EINVAL = 1,      /* bad size, non-finite or non-positive value, geometry off the grid */
+  TEM_ENOMEM = 2,      /* device allocation failed */
+  TEM_ENOCONV = 3,     /* some shift reached max_iter; outputs are still written */
+  TEM_EBREAKDOWN = 4,  /* COCG breakdown: (p, Ap) or (r, z) vanished or became non-finite */
+  TEM_ETIMEOUT = 5,    /* a bounded wait ran out */
+  TEM_ECUDA = 6,       /* a CUDA runtime call failed */
+  TEM_EBUSY = 7        /* serving: the request has not finished yet */
+};
+
+/* ---- precision of the shifted solves ----------------------------------- */
+enum {
+  TEM_PREC_FP64 = 0,   /* FP64 COCG sweeps */
+  TEM_PREC_MIXED = 1   /* FP32 COCG sweeps inside FP64 defect correction */
+};
+
+typedef struct tem_grid tem_grid;     /* opaque: device copy of the grid and conductivity */
+typedef struct tem_state tem_state;   /* opaque: kept shifted solutions of one forward call */
+
+/* Solver options.  Fill with tem_default_options() and then override. */
+typedef struct tem_options {
+  int32_t precision;     /* TEM_PREC_FP64 (default) or TEM_PREC_MIXED */
+  int32_t max_iter;      /* bound on COCG iterations per shift (default 20000) */
+  double tol;            /* stop when ||f - A_i x_i||_2 <= tol ||f||_2, FP64 residual (default 1e-12) */
+  double inner_tol;      /* MIXED: relative residual reduction per FP32 inner solve (default 1e-2) */
+  int32_t max_outer;     /* MIXED: bound on FP64 defect-correction steps (default 40) */
+  int32_t check_every;   /* iterations between host-side convergence polls (default 32) */
+  int32_t keep_state;    /* nonzero: keep the solutions for tem_adjoint (state_out must be non-NULL) */
+  int32_t reserved;
+} tem_options;
+
+/* Default options (see the field comments). */
+void tem_default_options(tem_options* opt);
+
+/* Name of a status code (static string). */
+const char* tem_status_string(int status);
+
+/* Library version string. */
+const char* tem_version(void);
+
+/*
+ * Install the device allocator used for every buffer the library creates.
+ * alloc(bytes, stream, ctx) returns a 256-byte aligned device pointer or NULL;
+ * release(ptr, bytes, stream, ctx) frees it.  Passing NULL for both restores
+ * cudaMallocAsync / cudaFreeAsync.  Not thread-safe with calls in flight.
+ */
+typedef void* (*tem_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
+typedef void (*tem_free_fn)(void* ptr, size_t bytes, void* cuda_stream, void* ctx);
+int tem_set_allocator(tem_alloc_fn alloc, tem_free_fn release, void* ctx);
+
+/*
+ * Build the device-side grid (Sec. 2.2: the discretisation of Eq. (pde)-(source)).
+ *   hx, hy, hz : cell widths, lengths nx, ny, nz >= 2, all finite and > 0.
+ *   origin     : 3 doubles, coordinates of node (0, 0, 0).
+ *   sigma      : nx*ny*nz cell conductivities (S/m), finite and > 0.
+ *   out        : receives the handle; release with tem_grid_destroy().
+ * Computes the lumped edge mass M_e = sum over the 4 cells containing e of
+ * sigma_c V_c / 4 (FP64 and an FP32 copy) and the 1-D face factors of K.
+ * Errors: TEM_EINVAL for bad sizes or values, TEM_ENOMEM, TEM_ECUDA.
+ */
+int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny,
+                   const double* hz, int64_t nz, const double* origin,
+                   const double* sigma, void* cuda_stream, tem_grid** out);
+
+/* Replace the conductivity of an existing grid (same sizes and rules as tem_build_grid). */
+int tem_grid_set_sigma(tem_grid* grid, const double* sigma, void* cuda_stream);
+
+/* Grid sizes: dims[0..2] = nx, ny, nz; returns TEM_EINVAL on NULL. */
+int tem_grid_dims(const tem_grid* grid, int64_t* dims);
+
+int tem_grid_destroy(tem_grid* grid);
+
+/*
+ * Shared poles and per-channel weights (Sec. 3.2, Eq. (ratfam)-(rkfit), (rmj)).
+ *   t        : K >= 1 channel times (s), finite, > 0, strictly increasing.
+ *   degree   : number of poles m-hat, 1 <= degree <= 64.
+ *   weights  : K positive weights w_k of the fit objective, or NULL for all ones.
+ *   xi       : out, 2*s doubles: the shifts (one pole of each conjugate pair,
+ *              with Im > 0, then the real poles), physical units (1/s).
+ *   c        : out, 2*s*K doubles, row-major [s][K]: c = 2 alpha for a pair,
+ *              alpha for a real pole, so that exp(-t_k lam) ~= sum_i Re(c[i,k] / (lam - xi_i)).
+ *              Caller allocates both with s = degree (an upper bound).
+ *   s_out    : out, the number of shifts s = ceil(degree / 2) for all-complex families.
+ *   uniform_err_out : out (may be NULL), Eq. (uniform_error): max_k w_k max_{x>=0} |e^{-t_k x} - r^[k](x)|
+ *              on a fine sample of [0, inf), in the normalised variable (t / t_max).
+ * The fit is the RKFIT pole relocation on a diagonal surrogate (times
+ * normalised by t_max), in FP64 on the host.  Errors: TEM_EINVAL.
+ */
+int tem_poles_residues(const double* t, int64_t K, int64_t degree, const double* weights,
+                       double* xi, double* c, int64_t* s_out, double* uniform_err_out);
+
+/*
+ * One step-off forward model (Eq. (rmjQ)):
+ *   d[r, k] = sum_i Re( c[i, k] q_r^T (K - xi_i M)^{-1} f ).
+ *   grid       : from tem_build_grid.
+ *   loop_xy    : n_vertices (x, y) pairs of a closed axis-aligned polygon
+ *                whose vertices are grid nodes, on the node plane z = z_loop;
+ *                counter-clockwise seen from +z gives a +z moment.
+ *   current    : loop current I (A).
+ *   rx_xyz     : n_rx receivers (x, y, z) inside the grid; z snaps to the
+ *                nearest node plane; d_t b_z is interpolated bilinearly
+ *                between z-face centres.  1 <= n_rx <= 4096.
+ *   xi, c, s, K: as returned by tem_poles_residues (1 <= s <= 64).
+ *   opt        : solver options (NULL = defaults).
+ *   dbzdt_out  : host, n_rx*K doubles, row-major [n_rx][K], d_t b_z in T/s.
+ *   state_out  : if opt->keep_state, receives the kept solutions for
+ *                tem_adjoint (release with tem_state_destroy); else may be NULL.
+ * Returns TEM_ENOCONV (output written) if a shift hit max_iter,
+ * TEM_EBREAKDOWN on a COCG breakdown, TEM_EINVAL on bad geometry.
+ */
+int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
+                double z_loop, double current, const double* rx_xyz, int64_t n_rx,
+                const double* xi, const double* c, int64_t s, int64_t K,
+                const tem_options* opt, void* cuda_stream, double* dbzdt_out,
+                tem_state** state_out);
+
+/*
+ * Per-shift diagnostics of the last forward (or adjoint) solve kept in `state`:
+ *   iters[s]   : COCG iterations (inner FP32 iterations summed, for MIXED),
+ *   relres[s]  : final FP64 relative residual ||f - A_i x_i|| / ||f||.
+ * Either pointer may be NULL.
+ */
+int tem_state_stats(const tem_state* state, int32_t* iters, double* relres);
+
+/*
+ * Adjoint gradient (Sec. 4): given g = dphi/dd (host, n_rx*K doubles laid
+ * out like dbzdt_out), writes grad[c] = dphi/dlog sigma_c for every cell
+ * (host, nx*ny*nz doubles):
+ *   beta[i, r] = sum_k c[i, k] g[r, k],   w_i = sum_r beta[i, r] q_r,
+ *   lambda_i = (K - xi_i M)^{-1} w_i      (A_i is complex symmetric),
+ *   grad[c] = sum_i Re( xi_i sum_{e in c} (sigma_c V_c / 4) lambda_i[e] x_i[e] ).
+ * The adjoint solves use the precision and tolerances of the forward call.
+ * Returns TEM_ENOCONV (gradient written) if an adjoint solve hit max_iter.
+ */
+int tem_adjoint(tem_state* state, const double* dphi_dd, void* cuda_stream, double* grad_logsigma_out);
+
+int tem_state_destroy(tem_state* state);
+
+/*
+ * Apply the shifted operator to s device vectors (the hot stencil, Sec. 2.2 K and M):
+ *   q[i] = (K - xi_i M) p[i],  i < s.
+ *   p_dev, q_dev : device, s complex vectors in the edge layout above, each
+ *                  3*nx*ny*nz complex entries; p's boundary entries must be 0,
+ *                  q's are written as 0.  FP64 (double2) if precision is
+ *                  TEM_PREC_FP64, FP32 (float2) if TEM_PREC_MIXED.
+ *   xi           : host, 2*s doubles.
+ * Enqueued on cuda_stream; returns without synchronising.
+ */
+int tem_apply_operator(const tem_grid* grid, const double* xi, int64_t s,
+                       const void* p_dev, void* q_dev, int32_t precision, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TEM_H_ */

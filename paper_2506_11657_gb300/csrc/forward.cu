@@ -1,0 +1,289 @@
+// tem_forward, tem_adjoint, tem_apply_operator: the C ABI over the batched solver.
+//
+// Forward (Eq. (rmjQ)):  d[r, k] = sum_i Re(c[i, k] q_r^T (K - xi_i M)^{-1} f).
+// Adjoint (Sec. 4):      grad[c] = sum_i Re(xi_i lambda_i^T (dM/dlog sigma_c) x_i),
+//                        lambda_i = (K - xi_i M)^{-1} sum_r beta[i, r] q_r,
+//                        beta[i, r] = sum_k c[i, k] g[r, k].
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+
+#include "kernels.cuh"
+#include "solver.h"
+
+using namespace tem;
+
+struct tem_state {
+  const tem_grid* grid = nullptr;
+  tem_options opt;
+  int s = 0, K = 0, n_rx = 0;
+  std::vector<double> xi, c;                // host copies
+  std::vector<int64_t> term_edge;
+  std::vector<double> term_w;
+  std::vector<int> term_off;
+  DevBuf sol;                               // per-slot vectors of the forward solve
+  std::unique_ptr<Batch> batch;             // forward batch (holds x_i)
+  std::vector<int32_t> iters;
+  std::vector<double> relres;
+};
+
+namespace {
+
+int validate_poles(const double* xi, const double* c, int64_t s, int64_t K) {
+  if (!xi || !c || s < 1 || s > 64 || K < 1 || K > 100000) return TEM_EINVAL;
+  for (int64_t q = 0; q < 2 * s; ++q)
+    if (!std::isfinite(xi[q])) return TEM_EINVAL;
+  for (int64_t q = 0; q < 2 * s * K; ++q)
+    if (!std::isfinite(c[q])) return TEM_EINVAL;
+  for (int64_t q = 0; q < s; ++q)
+    if (xi[2 * q] >= 0.0 && xi[2 * q + 1] == 0.0) return TEM_EINVAL;  // a real pole on [0, inf) makes A_i singular
+  return TEM_OK;
+}
+
+int validate_options(const tem_options& o) {
+  if (o.precision != TEM_PREC_FP64 && o.precision != TEM_PREC_MIXED) return TEM_EINVAL;
+  if (!(o.tol > 0.0 && o.tol < 1.0)) return TEM_EINVAL;
+  if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return TEM_EINVAL;
+  if (o.max_iter < 1 || o.max_outer < 1 || o.check_every < 1) return TEM_EINVAL;
+  return TEM_OK;
+}
+
+// Solve (K - xi_i M) x_i = b_i for all shifts of one grid; returns the batch.
+int solve_shifts(const tem_grid* g, const double* xi, int s, const tem_options& opt, cudaStream_t st,
+                 const double* f_dev, const void* rhs_c_dev, const double* bnorm2, DevBuf& vec,
+                 std::unique_ptr<Batch>& batch, SolveStats* stats) {
+  const int64_t ncomp = g->v.ncomp;
+  const size_t per = slot_vector_bytes(ncomp, opt.precision);
+  TEM_TRY(vec.alloc(per * s, st));
+  batch.reset(new Batch(opt.precision));
+  for (int i = 0; i < s; ++i) {
+    SlotVectors v = carve_slot(static_cast<char*>(vec.ptr) + per * i, ncomp, opt.precision);
+    const void* rc = rhs_c_dev ? static_cast<const char*>(rhs_c_dev) + (size_t)i * 3 * ncomp * 16 : nullptr;
+    TEM_TRY(batch->add_slot(g->v, xi[2 * i], xi[2 * i + 1], v, f_dev, rc));
+  }
+  TEM_TRY(batch->setup(opt, st, bnorm2));
+  return batch->solve(opt, st, stats);
+}
+
+int collect_status(const Batch& b, std::vector<int32_t>& iters, std::vector<double>& relres) {
+  int rc = TEM_OK;
+  iters.clear();
+  relres.clear();
+  for (const auto& S : b.scalars()) {
+    iters.push_back(S.total_iters);
+    relres.push_back(S.ff > 0 ? std::sqrt(S.rr64 / S.ff) : 0.0);
+    if (S.status == TEM_EBREAKDOWN) rc = TEM_EBREAKDOWN;
+    else if (S.status == TEM_ENOCONV && rc == TEM_OK) rc = TEM_ENOCONV;
+  }
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop, double current,
+                const double* rx_xyz, int64_t n_rx, const double* xi, const double* c, int64_t s, int64_t K,
+                const tem_options* opt_in, void* cuda_stream, double* dbzdt_out, tem_state** state_out) {
+  if (!grid || !dbzdt_out || !rx_xyz || n_rx < 1 || n_rx > 4096) return TEM_EINVAL;
+  if (state_out) *state_out = nullptr;
+  tem_options opt;
+  tem_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  TEM_TRY(validate_options(opt));
+  TEM_TRY(validate_poles(xi, c, s, K));
+  if (opt.keep_state && !state_out) return TEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  TEM_CUDA_TRY(cudaSetDevice(grid->device));
+  // source and receivers (sparse term lists, host)
+  std::vector<Term> fterms;
+  TEM_TRY(build_source(grid, loop_xy, n_vertices, z_loop, current, fterms));
+  std::unique_ptr<tem_state> S(new tem_state());
+  S->grid = grid;
+  S->opt = opt;
+  S->s = int(s);
+  S->K = int(K);
+  S->n_rx = int(n_rx);
+  S->xi.assign(xi, xi + 2 * s);
+  S->c.assign(c, c + 2 * s * K);
+  S->term_off.push_back(0);
+  for (int64_t r = 0; r < n_rx; ++r) {
+    std::vector<Term> q;
+    TEM_TRY(build_receiver(grid, rx_xyz + 3 * r, q));
+    for (auto& t : q) {
+      S->term_edge.push_back(t.edge);
+      S->term_w.push_back(t.w);
+    }
+    S->term_off.push_back((int)S->term_edge.size());
+  }
+  const int64_t ncomp = grid->v.ncomp;
+  // device: f (real, dense), the term lists, c and the output
+  DevBuf fbuf, misc;
+  const size_t nt = S->term_edge.size();
+  TEM_TRY(fbuf.alloc(3 * ncomp * sizeof(double), st));
+  const size_t misc_bytes = 256 + fterms.size() * 16 + nt * 16 + (n_rx + 1) * 8 + 2 * s * K * 8 + n_rx * K * 8 + 4096;
+  TEM_TRY(misc.alloc(misc_bytes, st));
+  char* m = misc.as<char>();
+  int64_t* d_fidx = reinterpret_cast<int64_t*>(m);
+  double* d_fval = reinterpret_cast<double*>(d_fidx + fterms.size());
+  int64_t* d_tedge = reinterpret_cast<int64_t*>(d_fval + fterms.size());
+  double* d_tw = reinterpret_cast<double*>(d_tedge + nt);
+  double* d_c = d_tw + nt;
+  double* d_out = d_c + 2 * s * K;
+  int* d_toff = reinterpret_cast<int*>(d_out + n_rx * K);
+  {
+    std::vector<int64_t> fi(fterms.size());
+    std::vector<double> fv(fterms.size());
+    double ff = 0.0;
+    for (size_t q = 0; q < fterms.size(); ++q) {
+      fi[q] = fterms[q].edge;
+      fv[q] = fterms[q].w;
+      ff += fv[q] * fv[q];
+    }
+    TEM_CUDA_TRY(cudaMemsetAsync(fbuf.ptr, 0, 3 * ncomp * sizeof(double), st));
+    if (!fi.empty()) {
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_fidx, fi.data(), fi.size() * 8, cudaMemcpyHostToDevice, st));
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_fval, fv.data(), fv.size() * 8, cudaMemcpyHostToDevice, st));
+    }
+    if (nt) {
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_tedge, S->term_edge.data(), nt * 8, cudaMemcpyHostToDevice, st));
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_tw, S->term_w.data(), nt * 8, cudaMemcpyHostToDevice, st));
+    }
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_toff, S->term_off.data(), (n_rx + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_c, c, 2 * s * K * 8, cudaMemcpyHostToDevice, st));
+    k_scatter<<<(int)((fi.size() + 255) / 256 + 1), 256, 0, st>>>(d_fidx, d_fval, (int64_t)fi.size(), fbuf.as<double>());
+    TEM_CUDA_TRY(cudaGetLastError());
+    std::vector<double> ffs(s, ff);
+    SolveStats stats;
+    int rc = solve_shifts(grid, xi, int(s), opt, st, fbuf.as<double>(), nullptr, ffs.data(), S->sol, S->batch, &stats);
+    if (rc != TEM_OK) return rc;
+  }
+  k_project_combine<<<(int)n_rx, 128, 0, st>>>(S->batch->slots_device(), S->batch->scalars_device(), int(s),
+                                                 d_tedge, d_tw, d_toff, d_c, int(K), d_out, int(n_rx));
+  TEM_CUDA_TRY(cudaGetLastError());
+  TEM_CUDA_TRY(cudaMemcpyAsync(dbzdt_out, d_out, n_rx * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TEM_CUDA_TRY(cudaStreamSynchronize(st));
+  const int rc = collect_status(*S->batch, S->iters, S->relres);
+  if (rc == TEM_EBREAKDOWN) return rc;
+  if (opt.keep_state) *state_out = S.release();
+  else if (state_out) *state_out = nullptr;
+  return rc;
+}
+
+int tem_state_stats(const tem_state* state, int32_t* iters, double* relres) {
+  if (!state) return TEM_EINVAL;
+  for (int i = 0; i < state->s; ++i) {
+    if (iters) iters[i] = state->iters[i];
+    if (relres) relres[i] = state->relres[i];
+  }
+  return TEM_OK;
+}
+
+int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) {
+  if (!S || !g || !grad || !S->batch) return TEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  for (int64_t q = 0; q < (int64_t)S->n_rx * S->K; ++q)
+    if (!std::isfinite(g[q])) return TEM_EINVAL;
+  const tem_grid* grid = S->grid;
+  const int64_t ncomp = grid->v.ncomp;
+  const int s = S->s, K = S->K, n_rx = S->n_rx;
+  // beta[i, r] = sum_k c[i, k] g[r, k];  w_i = sum_r beta[i, r] q_r (unique edges per slot)
+  std::vector<std::vector<std::pair<int64_t, std::pair<double, double>>>> w(s);
+  std::vector<double> ww(s, 0.0);
+  for (int i = 0; i < s; ++i) {
+    std::map<int64_t, std::pair<double, double>> acc;
+    for (int r = 0; r < n_rx; ++r) {
+      double br = 0.0, bi = 0.0;
+      for (int k = 0; k < K; ++k) {
+        br += S->c[2 * (i * K + k)] * g[r * K + k];
+        bi += S->c[2 * (i * K + k) + 1] * g[r * K + k];
+      }
+      for (int t = S->term_off[r]; t < S->term_off[r + 1]; ++t) {
+        auto& a = acc[S->term_edge[t]];
+        a.first += br * S->term_w[t];
+        a.second += bi * S->term_w[t];
+      }
+    }
+    for (auto& kv : acc) {
+      w[i].push_back({kv.first, kv.second});
+      ww[i] += kv.second.first * kv.second.first + kv.second.second * kv.second.second;
+    }
+  }
+  bool all_zero = true;
+  for (int i = 0; i < s; ++i) all_zero = all_zero && ww[i] == 0.0;
+  if (all_zero) {
+    std::memset(grad, 0, ncomp * sizeof(double));
+    return TEM_OK;
+  }
+  for (int i = 0; i < s; ++i)
+    if (ww[i] == 0.0) ww[i] = 1e-300;  // solve of a zero right-hand side ends at once
+  DevBuf rhs, vec;
+  TEM_TRY(rhs.alloc((size_t)s * 3 * ncomp * 16, st));
+  TEM_CUDA_TRY(cudaMemsetAsync(rhs.ptr, 0, (size_t)s * 3 * ncomp * 16, st));
+  {
+    std::vector<int64_t> idx;
+    std::vector<double> val;
+    for (int i = 0; i < s; ++i)
+      for (auto& e : w[i]) {
+        idx.push_back((int64_t)i * 3 * ncomp + e.first);
+        val.push_back(e.second.first);
+        val.push_back(e.second.second);
+      }
+    DevBuf tmp;
+    TEM_TRY(tmp.alloc(idx.size() * 8 + val.size() * 8 + 256, st));
+    int64_t* d_idx = tmp.as<int64_t>();
+    double* d_val = reinterpret_cast<double*>(d_idx + idx.size());
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st));
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_val, val.data(), val.size() * 8, cudaMemcpyHostToDevice, st));
+    k_scatter_c<<<(int)((idx.size() + 255) / 256 + 1), 256, 0, st>>>(d_idx, d_val, (int64_t)idx.size(), rhs.as<double>());
+    TEM_CUDA_TRY(cudaGetLastError());
+    TEM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  std::unique_ptr<Batch> ab;
+  SolveStats stats;
+  int rc = solve_shifts(grid, S->xi.data(), s, S->opt, st, nullptr, rhs.ptr, ww.data(), vec, ab, &stats);
+  if (rc != TEM_OK) return rc;
+  DevBuf gbuf;
+  TEM_TRY(gbuf.alloc(ncomp * sizeof(double), st));
+  k_gradient<<<152 * 8, 256, 0, st>>>(grid->v, grid->sig.as<double>(), S->batch->slots_device(),
+                                       S->batch->scalars_device(), ab->slots_device(), ab->scalars_device(), s,
+                                       gbuf.as<double>());
+  TEM_CUDA_TRY(cudaGetLastError());
+  TEM_CUDA_TRY(cudaMemcpyAsync(grad, gbuf.ptr, ncomp * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TEM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int32_t> it;
+  std::vector<double> rr;
+  return collect_status(*ab, it, rr);
+}
+
+int tem_state_destroy(tem_state* state) {
+  if (!state) return TEM_EINVAL;
+  cudaStreamSynchronize(state->sol.stream);
+  delete state;
+  return TEM_OK;
+}
+
+int tem_apply_operator(const tem_grid* grid, const double* xi, int64_t s, const void* p_dev, void* q_dev,
+                       int32_t precision, void* cuda_stream) {
+  if (!grid || !xi || !p_dev || !q_dev || s < 1 || s > 65535) return TEM_EINVAL;
+  if (precision != TEM_PREC_FP64 && precision != TEM_PREC_MIXED) return TEM_EINVAL;
+  for (int64_t q = 0; q < 2 * s; ++q)
+    if (!std::isfinite(xi[q])) return TEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  DevBuf dxi;
+  TEM_TRY(dxi.alloc(2 * s * sizeof(double), st));
+  TEM_CUDA_TRY(cudaMemcpyAsync(dxi.ptr, xi, 2 * s * sizeof(double), cudaMemcpyHostToDevice, st));
+  const GridView& g = grid->v;
+  const int zchunk = 32;
+  const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY, tz = (g.nz + zchunk - 1) / zchunk;
+  dim3 grd(tx * ty * tz, (unsigned)s);
+  if (precision == TEM_PREC_FP64)
+    k_apply<double><<<grd, NT, 0, st>>>(g, dxi.as<double>(), p_dev, q_dev, tx, ty, zchunk);
+  else
+    k_apply<float><<<grd, NT, 0, st>>>(g, dxi.as<double>(), p_dev, q_dev, tx, ty, zchunk);
+  TEM_CUDA_TRY(cudaGetLastError());
+  return TEM_OK;
+}
+
+}  // extern "C"

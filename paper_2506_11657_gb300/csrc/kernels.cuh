@@ -1,0 +1,688 @@
+// Device kernels of the batched shifted COCG on the Yee edge grid.
+//
+// Operator (Sec. 2.2, the Nedelec/Yee discretisation of Eq. (pde)):
+//   (A_i p)_e = (K p)_e - xi_i M_e p_e,
+//   (K p)_e   = L_e * sum_{faces f containing e} (+-) F_f,
+//   F_f       = (L*_f / mu0) * circ_f(p) / A_f   (written below with 1/L factors),
+// with circ_f the signed sum of L_e p_e around face f.  For the face whose
+// normal is +x at node (i, j, k):
+//   F_x = (Sx_i/mu0) [ (p_y(i,j,k) - p_y(i,j,k+1)) / Lz_k + (p_z(i,j+1,k) - p_z(i,j,k)) / Ly_j ]
+//   F_y = (Sy_j/mu0) [ (p_z(i,j,k) - p_z(i+1,j,k)) / Lx_i + (p_x(i,j,k+1) - p_x(i,j,k)) / Lz_k ]
+//   F_z = (Sz_k/mu0) [ (p_x(i,j,k) - p_x(i,j+1,k)) / Ly_j + (p_y(i+1,j,k) - p_y(i,j,k)) / Lx_i ]
+// and the edges leaving node (i, j, k):
+//   (Kp)_x = Lx_i [ F_z(i,j,k) - F_z(i,j-1,k) - F_y(i,j,k) + F_y(i,j,k-1) ]
+//   (Kp)_y = Ly_j [ F_x(i,j,k) - F_x(i,j,k-1) - F_z(i,j,k) + F_z(i-1,j,k) ]
+//   (Kp)_z = Lz_k [ F_y(i,j,k) - F_y(i-1,j,k) - F_x(i,j,k) + F_x(i,j-1,k) ]
+// Edges in the boundary (n x e = 0, Eq. (bc)) are held at zero.
+//
+// Tiling: a CTA owns a TX x TY column of nodes and marches a chunk of z
+// planes.  Plane k and k+1 of the input vector (with a one-node halo) live in
+// shared memory; the faces of plane k are computed once into shared memory;
+// the faces of plane k-1 that an edge needs stay in registers.
+#pragma once
+
+#include "tem_internal.h"
+
+namespace tem {
+
+// ---------------------------------------------------------------- complex
+template <class T> struct C2 {
+  T re, im;
+  __host__ __device__ C2() {}
+  __host__ __device__ C2(T r, T i) : re(r), im(i) {}
+};
+template <class T> __device__ __forceinline__ C2<T> operator+(C2<T> a, C2<T> b) { return C2<T>(a.re + b.re, a.im + b.im); }
+template <class T> __device__ __forceinline__ C2<T> operator-(C2<T> a, C2<T> b) { return C2<T>(a.re - b.re, a.im - b.im); }
+template <class T> __device__ __forceinline__ C2<T> operator*(T s, C2<T> a) { return C2<T>(s * a.re, s * a.im); }
+template <class T> __device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return C2<T>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class T> __device__ __forceinline__ C2<T> cdiv(C2<T> a, C2<T> b) {
+  T d = T(1) / (b.re * b.re + b.im * b.im);
+  return C2<T>((a.re * b.re + a.im * b.im) * d, (a.im * b.re - a.re * b.im) * d);
+}
+template <class T> __device__ __forceinline__ C2<T> czero() { return C2<T>(T(0), T(0)); }
+
+template <class T> struct Vec2;
+template <> struct Vec2<float> { typedef float2 type; };
+template <> struct Vec2<double> { typedef double2 type; };
+
+template <class T> __device__ __forceinline__ C2<T> ld(const void* base, int64_t idx) {
+  typedef typename Vec2<T>::type V;
+  V v = __ldg(reinterpret_cast<const V*>(base) + idx);
+  return C2<T>(v.x, v.y);
+}
+template <class T> __device__ __forceinline__ void st(void* base, int64_t idx, C2<T> a) {
+  typedef typename Vec2<T>::type V;
+  V v; v.x = a.re; v.y = a.im;
+  reinterpret_cast<V*>(base)[idx] = v;
+}
+
+// 1-D geometry accessors in the working precision
+template <class T> struct Geo;
+template <> struct Geo<double> {
+  const double *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Me;
+  __device__ Geo(const GridView& g) : Lx(g.Lx), Ly(g.Ly), Lz(g.Lz), Sx(g.Sx), Sy(g.Sy), Sz(g.Sz), Me(g.Me) {}
+};
+template <> struct Geo<float> {
+  const float *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Me;
+  __device__ Geo(const GridView& g) : Lx(g.Lxf), Ly(g.Lyf), Lz(g.Lzf), Sx(g.Sxf), Sy(g.Syf), Sz(g.Szf), Me(g.Mef) {}
+};
+
+// Diagonal of K at edge (c, i, j, k) (valid, non-boundary edges only):
+//   x: Lx_i/mu0 [ Sz_k (1/Ly_j + 1/Ly_{j-1}) + Sy_j (1/Lz_k + 1/Lz_{k-1}) ]   and cyclically.
+template <class T>
+__device__ __forceinline__ T diagK(const Geo<T>& G, int c, int i, int j, int k) {
+  const T inv_mu0 = T(1.0 / TEM_MU0);
+  if (c == 0)
+    return G.Lx[i] * inv_mu0 * (G.Sz[k] * (T(1) / G.Ly[j] + T(1) / G.Ly[j - 1]) + G.Sy[j] * (T(1) / G.Lz[k] + T(1) / G.Lz[k - 1]));
+  if (c == 1)
+    return G.Ly[j] * inv_mu0 * (G.Sz[k] * (T(1) / G.Lx[i] + T(1) / G.Lx[i - 1]) + G.Sx[i] * (T(1) / G.Lz[k] + T(1) / G.Lz[k - 1]));
+  return G.Lz[k] * inv_mu0 * (G.Sx[i] * (T(1) / G.Ly[j] + T(1) / G.Ly[j - 1]) + G.Sy[j] * (T(1) / G.Lx[i] + T(1) / G.Lx[i - 1]));
+}
+
+// Is edge (c, i, j, k) an unknown (not in the boundary, not padding)?
+__device__ __forceinline__ bool edge_valid(int c, int i, int j, int k) {
+  return c == 0 ? (j > 0 && k > 0) : (c == 1 ? (i > 0 && k > 0) : (i > 0 && j > 0));
+}
+
+// ------------------------------------------------------- deterministic reductions
+// Each CTA writes its partial sums to part[slot * stride + local_block]; the last
+// CTA of the slot to finish (counted with an atomic ticket) sums them in block
+// order, so the result does not depend on scheduling.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh) {
+  // warp shuffle, then one value per warp through shared memory, in fixed order
+  for (int q = 0; q < NV; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+    for (int q = 0; q < NV; ++q) sh[warp * NV + q] = v[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NV; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < NT / 32; ++w) s += sh[w * NV + q];
+      v[q] = s;
+    }
+  }
+}
+
+// Returns true in thread 0 of the last CTA of the slot, after which part[] of
+// the slot is complete and visible.
+template <int NV>
+__device__ __forceinline__ bool publish_partial(const double (&v)[NV], double* part, unsigned* ticket,
+                                                int nblk, int lb) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NV; ++q) part[(int64_t)lb * NV + q] = v[q];
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    last = (t == (unsigned)nblk - 1u);
+    if (last) {
+      *ticket = 0u;
+      __threadfence();
+    }
+  }
+  __syncthreads();
+  return last;
+}
+
+// Sum the slot's partials with the whole CTA: thread t adds blocks t, t+NT, ...
+// in order, then the fixed shuffle tree; the result lands in thread 0.
+template <int NV, int NTH>
+__device__ __forceinline__ void sum_partials(const double* part, int nblk, double (&out)[NV], double* sh) {
+  for (int q = 0; q < NV; ++q) out[q] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += NTH)
+    for (int q = 0; q < NV; ++q) out[q] += __ldcg(part + (int64_t)b * NV + q);
+  block_sum<NV, NTH>(out, sh);
+}
+
+// ------------------------------------------------------------- stencil core
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int NT = TX * TY;
+constexpr int PX = TX + 2;   // plane tile with halo (-1 .. TX)
+constexpr int PY = TY + 2;
+constexpr int FX = TX + 1;   // face tile (-1 .. TX-1)
+constexpr int FY = TY + 1;
+
+template <class T>
+struct StencilSmem {
+  C2<T> P[2][3][PY][PX];
+  C2<T> F[3][FY][FX];
+  double red[NT / 32 * 4];
+};
+
+// Load plane k of the input into buffer b through the policy's point loader.
+template <class T, class Pol>
+__device__ __forceinline__ void load_plane(StencilSmem<T>& sm, int b, int k, int i0, int j0,
+                                           const GridView& g, Pol& pol, bool own_plane) {
+  for (int t = threadIdx.x; t < 3 * PY * PX; t += NT) {
+    const int c = t / (PY * PX);
+    const int r = t - c * (PY * PX);
+    const int jj = r / PX, ii = r - jj * PX;
+    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+    C2<T> v = czero<T>();
+    if (k >= 0 && k < g.nz && i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
+      const int64_t idx = (int64_t)c * g.ncomp + i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+      const bool own = own_plane && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY;
+      v = pol.load(idx, own);
+    }
+    sm.P[b][c][jj][ii] = v;
+  }
+}
+
+// Faces of plane k (buffer bk) using plane k+1 (buffer bk1), for the tile plus its -1 halo.
+template <class T>
+__device__ __forceinline__ void compute_faces(StencilSmem<T>& sm, int bk, int bk1, int k, int i0, int j0,
+                                              const GridView& g, const Geo<T>& G) {
+  const T inv_mu0 = T(1.0 / TEM_MU0);
+  for (int t = threadIdx.x; t < FY * FX; t += NT) {
+    const int jj = t / FX, ii = t - jj * FX;
+    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+    C2<T> fx = czero<T>(), fy = czero<T>(), fz = czero<T>();
+    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
+      const T rLx = T(1) / G.Lx[i], rLy = T(1) / G.Ly[j], rLz = T(1) / G.Lz[k];
+      // plane-k values around (ii, jj)
+      const C2<T> px = sm.P[bk][0][jj][ii], py = sm.P[bk][1][jj][ii], pz = sm.P[bk][2][jj][ii];
+      const C2<T> pz_j1 = sm.P[bk][2][jj + 1][ii];
+      const C2<T> pz_i1 = sm.P[bk][2][jj][ii + 1];
+      const C2<T> px_j1 = sm.P[bk][0][jj + 1][ii];
+      const C2<T> py_i1 = sm.P[bk][1][jj][ii + 1];
+      const C2<T> px_k1 = sm.P[bk1][0][jj][ii];
+      const C2<T> py_k1 = sm.P[bk1][1][jj][ii];
+      fx = (G.Sx[i] * inv_mu0) * (rLz * (py - py_k1) + rLy * (pz_j1 - pz));
+      fy = (G.Sy[j] * inv_mu0) * (rLx * (pz - pz_i1) + rLz * (px_k1 - px));
+      fz = (G.Sz[k] * inv_mu0) * (rLy * (px - px_j1) + rLx * (py_i1 - py));
+    }
+    sm.F[0][jj][ii] = fx;
+    sm.F[1][jj][ii] = fy;
+    sm.F[2][jj][ii] = fz;
+  }
+}
+
+// Own faces F_x, F_y of plane k for thread (a, b), straight from the planes.
+template <class T>
+__device__ __forceinline__ void own_faces_xy(const StencilSmem<T>& sm, int bk, int bk1, int k, int i, int j,
+                                             int ii, int jj, const GridView& g, const Geo<T>& G,
+                                             C2<T>& fx, C2<T>& fy) {
+  fx = czero<T>();
+  fy = czero<T>();
+  if (k < 0 || k >= g.nz || i >= g.nx || j >= g.ny) return;
+  const T inv_mu0 = T(1.0 / TEM_MU0);
+  const T rLx = T(1) / G.Lx[i], rLy = T(1) / G.Ly[j], rLz = T(1) / G.Lz[k];
+  const C2<T> px = sm.P[bk][0][jj][ii], py = sm.P[bk][1][jj][ii], pz = sm.P[bk][2][jj][ii];
+  fx = (G.Sx[i] * inv_mu0) * (rLz * (py - sm.P[bk1][1][jj][ii]) + rLy * (sm.P[bk][2][jj + 1][ii] - pz));
+  fy = (G.Sy[j] * inv_mu0) * (rLx * (pz - sm.P[bk][2][jj][ii + 1]) + rLz * (sm.P[bk1][0][jj][ii] - px));
+}
+
+// The z-marching stencil: for every own valid edge of planes [k0, k1) calls
+// pol.edge(c, idx, i, j, k, p_e, (Kp)_e).  Invalid own edges get pol.edge_invalid(idx).
+template <class T, class Pol>
+__device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView& g, Pol& pol,
+                                              int i0, int j0, int k0, int k1) {
+  const Geo<T> G(g);
+  const int a = threadIdx.x % TX, b = threadIdx.x / TX;
+  const int i = i0 + a, j = j0 + b;
+  const int ii = a + 1, jj = b + 1;
+  // prologue: planes k0-1 (buffer 0) and k0 (buffer 1)
+  load_plane<T>(sm, 0, k0 - 1, i0, j0, g, pol, false);
+  load_plane<T>(sm, 1, k0, i0, j0, g, pol, true);
+  __syncthreads();
+  C2<T> fxm, fym;  // F_x, F_y of plane k-1 at (i, j)
+  own_faces_xy<T>(sm, 0, 1, k0 - 1, i, j, ii, jj, g, G, fxm, fym);
+  int bk = 1;  // buffer of plane k
+  for (int k = k0; k < k1; ++k) {
+    const int bk1 = bk ^ 1;
+    __syncthreads();  // buffer bk1 (plane k-1) and F are free
+    load_plane<T>(sm, bk1, k + 1, i0, j0, g, pol, k + 1 < k1);
+    __syncthreads();
+    compute_faces<T>(sm, bk, bk1, k, i0, j0, g, G);
+    __syncthreads();
+    if (i < g.nx && j < g.ny) {
+      const int64_t base = i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+      const C2<T> fx = sm.F[0][jj][ii], fy = sm.F[1][jj][ii], fz = sm.F[2][jj][ii];
+      // x-edge
+      if (edge_valid(0, i, j, k)) {
+        const C2<T> kp = G.Lx[i] * ((fz - sm.F[2][jj - 1][ii]) - (fy - fym));
+        pol.edge(0, base, i, j, k, sm.P[bk][0][jj][ii], kp);
+      } else {
+        pol.edge_invalid(base);
+      }
+      if (edge_valid(1, i, j, k)) {
+        const C2<T> kp = G.Ly[j] * ((fx - fxm) - (fz - sm.F[2][jj][ii - 1]));
+        pol.edge(1, g.ncomp + base, i, j, k, sm.P[bk][1][jj][ii], kp);
+      } else {
+        pol.edge_invalid(g.ncomp + base);
+      }
+      if (edge_valid(2, i, j, k)) {
+        const C2<T> kp = G.Lz[k] * ((fy - sm.F[1][jj][ii - 1]) - (fx - sm.F[0][jj - 1][ii]));
+        pol.edge(2, 2 * g.ncomp + base, i, j, k, sm.P[bk][2][jj][ii], kp);
+      } else {
+        pol.edge_invalid(2 * g.ncomp + base);
+      }
+      fxm = fx;
+      fym = fy;
+    }
+    bk = bk1;
+  }
+}
+
+// --------------------------------------------------------------- slot plumbing
+struct BatchArgs {
+  const SlotDesc* slots;
+  SlotScalars* sc;
+  const int* blk2slot;       // stencil launch: CTA -> slot
+  const int* ublk2slot;      // update launch: CTA -> slot
+  double* part;              // [slot][maxblk][4]
+  unsigned* ticket;          // [slot]
+  int* n_active;             // slots still iterating
+  int part_stride;           // doubles per slot in part
+  int zchunk;                // planes per stencil CTA
+};
+
+__device__ __forceinline__ void tile_of(const SlotDesc& d, int lb, int zchunk, int nz,
+                                        int& i0, int& j0, int& k0, int& k1) {
+  const int tx = lb % d.tiles_x;
+  const int r = lb / d.tiles_x;
+  const int ty = r % d.tiles_y;
+  const int zc = r / d.tiles_y;
+  i0 = tx * TX;
+  j0 = ty * TY;
+  k0 = zc * zchunk;
+  k1 = min(k0 + zchunk, nz);
+}
+
+// ---------------------------------------------------- pass 1: p <- z + beta p; q <- A p
+template <class T>
+struct CocgStencilPol {
+  const void* z; const void* pold; void* pnew; void* q;
+  C2<T> beta; bool use_beta;
+  C2<T> xi;
+  const T* Me;
+  C2<T> acc;
+  __device__ C2<T> load(int64_t idx, bool own) {
+    C2<T> v = ld<T>(z, idx);
+    if (use_beta) v = v + cmul(beta, ld<T>(pold, idx));
+    if (own) st<T>(pnew, idx, v);
+    return v;
+  }
+  __device__ void edge(int, int64_t idx, int, int, int, C2<T> p, C2<T> kp) {
+    const C2<T> qv = kp - cmul(xi, Me[idx] * p);
+    st<T>(q, idx, qv);
+    acc = acc + cmul(p, qv);
+  }
+  __device__ void edge_invalid(int64_t idx) { st<T>(q, idx, czero<T>()); }
+};
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_cocg_stencil(BatchArgs A) {
+  __shared__ StencilSmem<T> sm;
+  const int slot = A.blk2slot[blockIdx.x];
+  SlotScalars* S = A.sc + slot;
+  if (!S->active) return;
+  const SlotDesc d = A.slots[slot];
+  const int lb = blockIdx.x - d.blk_stencil0;
+  int i0, j0, k0, k1;
+  tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
+  CocgStencilPol<T> pol;
+  pol.z = d.z;
+  pol.pold = S->parity ? d.p1 : d.p0;
+  pol.pnew = S->parity ? d.p0 : d.p1;
+  pol.q = d.q;
+  pol.beta = C2<T>(T(S->beta_re), T(S->beta_im));
+  pol.use_beta = !(S->beta_re == 0.0 && S->beta_im == 0.0);
+  pol.xi = C2<T>(T(d.xi_re), T(d.xi_im));
+  pol.Me = Geo<T>(d.g).Me;
+  pol.acc = czero<T>();
+  stencil_march<T>(sm, d.g, pol, i0, j0, k0, k1);
+  double v[2] = {double(pol.acc.re), double(pol.acc.im)};
+  block_sum<2, NT>(v, sm.red);
+  double* part = A.part + (int64_t)slot * A.part_stride;
+  if (publish_partial<2>(v, part, A.ticket + slot, d.nblk_stencil, lb)) {
+    double tot[2];
+    sum_partials<2, NT>(part, d.nblk_stencil, tot, sm.red);
+    if (threadIdx.x != 0) return;
+    // alpha = rho / (p, A p)
+    const double den = tot[0] * tot[0] + tot[1] * tot[1];
+    if (!(den > 0.0) || !isfinite(den)) {
+      S->status = TEM_EBREAKDOWN;
+      S->active = 0;
+      atomicSub(A.n_active, 1);
+    } else {
+      S->alpha_re = (S->rho_re * tot[0] + S->rho_im * tot[1]) / den;
+      S->alpha_im = (S->rho_im * tot[0] - S->rho_re * tot[1]) / den;
+    }
+  }
+}
+
+// ------------------------------------- pass 2: x += alpha p; r -= alpha q; z = r / D
+// r itself is not stored: r = D z is rebuilt from the stored preconditioned residual.
+template <class T>
+__global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
+  __shared__ double red[NT / 32 * 4];
+  const int slot = A.ublk2slot[blockIdx.x];
+  SlotScalars* S = A.sc + slot;
+  if (!S->active) return;
+  const SlotDesc d = A.slots[slot];
+  const int lb = blockIdx.x - d.blk_update0;
+  const GridView& g = d.g;
+  const Geo<T> G(g);
+  const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
+  const C2<T> xi(T(d.xi_re), T(d.xi_im));
+  const bool first = d.x_fresh && S->iters == 0;  // MIXED: the correction starts at 0
+  const void* p = S->parity ? d.p0 : d.p1;  // the direction written by pass 1
+  C2<T> rz = czero<T>();
+  T rr = T(0);
+  // each CTA owns a contiguous range of entries of the slot; entry e = row * nx + i with
+  // row = c * ny * nz + k * ny + j
+  const uint32_t n = (uint32_t)(3 * g.ncomp);
+  const uint32_t per = (n + d.nblk_update - 1) / d.nblk_update;
+  const uint32_t e0 = (uint32_t)lb * per, e1 = min(n, e0 + per);
+  for (uint32_t e = e0 + threadIdx.x; e < e1; e += NT) {
+    const uint32_t row = fdiv(e, d.div_nx);
+    const int i = int(e - row * (uint32_t)g.nx);
+    const uint32_t c = fdiv(row, d.div_nynz);
+    const uint32_t jk = row - c * (uint32_t)(g.ny * g.nz);
+    const uint32_t k = fdiv(jk, d.div_ny);
+    const int j = int(jk - k * (uint32_t)g.ny);
+    if (!edge_valid(int(c), i, j, int(k))) continue;
+    const C2<T> D = C2<T>(diagK<T>(G, int(c), i, j, int(k)), T(0)) - (G.Me[e] * xi);
+    const C2<T> pv = ld<T>(p, e);
+    const C2<T> qv = ld<T>(d.q, e);
+    C2<T> r = cmul(D, ld<T>(d.z, e));
+    r = r - cmul(alpha, qv);
+    C2<T> xv = cmul(alpha, pv);
+    if (!first) xv = xv + ld<T>(d.x, e);
+    st<T>(d.x, e, xv);
+    const C2<T> zv = cdiv(r, D);
+    st<T>(d.z, e, zv);
+    rz = rz + cmul(r, zv);
+    rr += r.re * r.re + r.im * r.im;
+  }
+  double v[3] = {double(rz.re), double(rz.im), double(rr)};
+  block_sum<3, NT>(v, red);
+  double* part = A.part + (int64_t)slot * A.part_stride;
+  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_update, lb)) {
+    double tot[3];
+    sum_partials<3, NT>(part, d.nblk_update, tot, red);
+    if (threadIdx.x != 0) return;
+    S->iters += 1;
+    S->rr = tot[2];
+    bool done = false;
+    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
+      S->status = TEM_EBREAKDOWN;
+      done = true;
+    } else if (tot[2] <= S->tol2) {
+      done = true;  // converged
+    } else if (S->iters >= S->max_iter) {
+      S->status = TEM_ENOCONV;
+      done = true;
+    } else {
+      const double den = S->rho_re * S->rho_re + S->rho_im * S->rho_im;
+      if (!(den > 0.0)) {
+        S->status = TEM_EBREAKDOWN;
+        done = true;
+      } else {
+        S->beta_re = (tot[0] * S->rho_re + tot[1] * S->rho_im) / den;
+        S->beta_im = (tot[1] * S->rho_re - tot[0] * S->rho_im) / den;
+        S->rho_re = tot[0];
+        S->rho_im = tot[1];
+        S->parity ^= 1;
+      }
+    }
+    if (done) {
+      S->active = 0;
+      S->total_iters += S->iters;
+      atomicSub(A.n_active, 1);
+    }
+  }
+}
+
+
+// ------------------------------- FP64 residual pass (the outer defect-correction step)
+// x <- x64[cur] (+ inv_scale_prev * delta for MIXED, written to x64[cur^1]);
+// r = b - A x in FP64;  z_inner = (scale r) / D  in the inner precision TI;
+// then (last CTA) either finish the slot or arm the next inner COCG solve.
+template <class TI>
+struct ResidualPol {
+  const void* xcur; const void* delta; void* xnext; double inv_sc; bool upd;
+  const double* f; const void* rhs_c;
+  C2<double> xi; const double* Me;
+  Geo<TI> GI; TI xi_re_i, xi_im_i;
+  void* z; double scale;
+  double rr, rz_re, rz_im;
+  __device__ ResidualPol(const GridView& g) : GI(g) {}
+  __device__ C2<double> load(int64_t idx, bool own) {
+    C2<double> x = ld<double>(xcur, idx);
+    if (upd) {
+      const C2<TI> dv = ld<TI>(delta, idx);
+      x = x + inv_sc * C2<double>(double(dv.re), double(dv.im));
+      if (own) st<double>(xnext, idx, x);
+    }
+    return x;
+  }
+  __device__ void edge(int c, int64_t idx, int i, int j, int k, C2<double> xv, C2<double> kx) {
+    const C2<double> ax = kx - cmul(xi, Me[idx] * xv);
+    const C2<double> b = rhs_c ? ld<double>(rhs_c, idx) : C2<double>(f[idx], 0.0);
+    const C2<double> r = b - ax;
+    rr += r.re * r.re + r.im * r.im;
+    const C2<TI> rs(TI(scale * r.re), TI(scale * r.im));
+    const C2<TI> D = C2<TI>(diagK<TI>(GI, c, i, j, k), TI(0)) - (GI.Me[idx] * C2<TI>(xi_re_i, xi_im_i));
+    const C2<TI> zv = cdiv(rs, D);
+    st<TI>(z, idx, zv);
+    const C2<TI> p = cmul(rs, zv);
+    rz_re += double(p.re);
+    rz_im += double(p.im);
+  }
+  __device__ void edge_invalid(int64_t idx) { st<TI>(z, idx, czero<TI>()); }
+};
+
+template <class TI>
+__global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
+  __shared__ StencilSmem<double> sm;
+  const int slot = A.blk2slot[blockIdx.x];
+  SlotScalars* S = A.sc + slot;
+  if (S->done || S->active) return;  // finished, or its inner solve is still running
+  const SlotDesc d = A.slots[slot];
+  const int lb = blockIdx.x - d.blk_stencil0;
+  int i0, j0, k0, k1;
+  tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
+  ResidualPol<TI> pol(d.g);
+  pol.upd = d.x_fresh && S->outer > 0;
+  pol.xcur = d.x64[S->xcur];
+  pol.xnext = d.x64[S->xcur ^ 1];
+  pol.delta = d.x;
+  pol.inv_sc = S->inv_scale_prev;
+  pol.f = d.f;
+  pol.rhs_c = d.rhs_c;
+  pol.xi = C2<double>(d.xi_re, d.xi_im);
+  pol.Me = d.g.Me;
+  pol.xi_re_i = TI(d.xi_re);
+  pol.xi_im_i = TI(d.xi_im);
+  pol.z = d.z;
+  pol.scale = S->scale;
+  pol.rr = pol.rz_re = pol.rz_im = 0.0;
+  stencil_march<double>(sm, d.g, pol, i0, j0, k0, k1);
+  double v[3] = {pol.rr, pol.rz_re, pol.rz_im};
+  block_sum<3, NT>(v, sm.red);
+  double* part = A.part + (int64_t)slot * A.part_stride;
+  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_stencil, lb)) {
+    double tot[3];
+    sum_partials<3, NT>(part, d.nblk_stencil, tot, sm.red);
+    if (threadIdx.x != 0) return;
+    if (pol.upd) S->xcur ^= 1;
+    S->rr64 = tot[0];
+    S->outer += 1;
+    bool finish = false;
+    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
+      S->status = TEM_EBREAKDOWN;
+      finish = true;
+    } else if (tot[0] <= S->tol_outer2) {
+      finish = true;
+    } else if (S->status != TEM_OK) {
+      finish = true;  // the last inner solve failed
+    } else if (S->outer > S->max_outer || S->total_iters >= S->max_iter) {
+      S->status = TEM_ENOCONV;
+      finish = true;
+    }
+    if (finish) {
+      S->done = 1;
+      atomicAdd(n_done, 1);
+      return;
+    }
+    // arm the inner solve on  A delta = scale * r  (MIXED)  or continue x (FP64)
+    const double sc = S->scale;
+    S->bb = sc * sc * tot[0];
+    const double want = 0.25 * S->tol_outer2 / tot[0];   // reach 1/2 of the final target
+    const double rel2 = d.x_fresh ? fmax(S->inner_rel2, want) : want;
+    S->tol2 = rel2 * S->bb;
+    S->rho_re = tot[1];
+    S->rho_im = tot[2];
+    S->beta_re = 0.0;
+    S->beta_im = 0.0;
+    S->iters = 0;
+    S->parity = 0;
+    S->inv_scale_prev = 1.0 / sc;
+    if (d.x_fresh) S->scale = 1.0 / sqrt(tot[0]);
+    S->active = 1;
+    atomicAdd(A.n_active, 1);
+  }
+}
+
+// ------------------------------------------------------ q = (K - xi M) p, s shifts
+template <class T>
+struct ApplyPol {
+  const void* p; void* q; C2<T> xi; const T* Me;
+  __device__ C2<T> load(int64_t idx, bool) { return ld<T>(p, idx); }
+  __device__ void edge(int, int64_t idx, int, int, int, C2<T> pv, C2<T> kp) {
+    st<T>(q, idx, kp - cmul(xi, Me[idx] * pv));
+  }
+  __device__ void edge_invalid(int64_t idx) { st<T>(q, idx, czero<T>()); }
+};
+
+template <class T>
+__global__ void __launch_bounds__(NT) k_apply(GridView g, const double* xi, const void* p, void* q,
+                                              int tiles_x, int tiles_y, int zchunk) {
+  __shared__ StencilSmem<T> sm;
+  const int shift = blockIdx.y;
+  const int lb = blockIdx.x;
+  const int tx = lb % tiles_x, r = lb / tiles_x, ty = r % tiles_y, zc = r / tiles_y;
+  const int i0 = tx * TX, j0 = ty * TY, k0 = zc * zchunk, k1 = min(k0 + zchunk, g.nz);
+  const int64_t n = 3 * g.ncomp;
+  typedef typename Vec2<T>::type V;
+  ApplyPol<T> pol;
+  pol.p = reinterpret_cast<const V*>(p) + shift * n;
+  pol.q = reinterpret_cast<V*>(q) + shift * n;
+  pol.xi = C2<T>(T(xi[2 * shift]), T(xi[2 * shift + 1]));
+  pol.Me = Geo<T>(g).Me;
+  stencil_march<T>(sm, g, pol, i0, j0, k0, k1);
+}
+
+// --------------------------------- receivers and the pole -> channel combination
+// y[i][r] = sum_terms w x_i[edge];   d[r][k] = sum_i Re(c[i][k] y[i][r])   (Eq. (rmjQ))
+static __global__ void k_project_combine(const SlotDesc* slots, const SlotScalars* sc, int s,
+                                  const int64_t* term_edge, const double* term_w, const int* term_off,
+                                  const double* c, int K, double* d, int n_rx) {
+  __shared__ double ys[2 * 64];
+  const int r = blockIdx.x;
+  if (r >= n_rx) return;
+  const int t0 = term_off[r], t1 = term_off[r + 1];
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    const SlotDesc& dsc = slots[i];
+    const void* x = dsc.x64[sc[i].xcur];
+    double yr = 0.0, yi = 0.0;
+    for (int t = t0; t < t1; ++t) {
+      const C2<double> v = ld<double>(x, term_edge[t]);
+      yr += term_w[t] * v.re;
+      yi += term_w[t] * v.im;
+    }
+    ys[2 * i] = yr;
+    ys[2 * i + 1] = yi;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < s; ++i) {
+      const double cr = c[2 * (i * K + k)], ci = c[2 * (i * K + k) + 1];
+      acc += cr * ys[2 * i] - ci * ys[2 * i + 1];
+    }
+    d[(int64_t)r * K + k] = acc;
+  }
+}
+
+// y[i][r] alone (diagnostics and the cancellation factor)
+static __global__ void k_project(const SlotDesc* slots, const SlotScalars* sc, int s,
+                          const int64_t* term_edge, const double* term_w, const int* term_off,
+                          double* y, int n_rx) {
+  const int r = blockIdx.x;
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    const void* x = slots[i].x64[sc[i].xcur];
+    double yr = 0.0, yi = 0.0;
+    for (int t = term_off[r]; t < term_off[r + 1]; ++t) {
+      const C2<double> v = ld<double>(x, term_edge[t]);
+      yr += term_w[t] * v.re;
+      yi += term_w[t] * v.im;
+    }
+    y[2 * ((int64_t)i * n_rx + r)] = yr;
+    y[2 * ((int64_t)i * n_rx + r) + 1] = yi;
+  }
+}
+
+// ------------------------------------------------------------- scatters
+static __global__ void k_scatter(const int64_t* idx, const double* val, int64_t n, double* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[idx[t]] = val[t];
+}
+static __global__ void k_scatter_c(const int64_t* idx, const double* val, int64_t n, double* out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    out[2 * idx[t]] = val[2 * t];
+    out[2 * idx[t] + 1] = val[2 * t + 1];
+  }
+}
+
+// ------------------------------------------------------------- adjoint gradient
+// g[cell] = sum_i Re( xi_i sigma_c V_c / 4 sum_{12 edges e of the cell} lam_i[e] x_i[e] )
+static __global__ void k_gradient(GridView g, const double* sigma, const SlotDesc* fwd, const SlotScalars* fsc,
+                           const SlotDesc* adj, const SlotScalars* asc, int s, double* grad) {
+  const int64_t ncell = g.ncomp;
+  for (int64_t cidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; cidx < ncell;
+       cidx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = int(cidx % g.nx);
+    const int64_t r = cidx / g.nx;
+    const int j = int(r % g.ny), k = int(r / g.ny);
+    const double q = 0.25 * sigma[cidx] * g.Lx[i] * g.Ly[j] * g.Lz[k];
+    double acc = 0.0;
+    for (int sh = 0; sh < s; ++sh) {
+      const void* x = fwd[sh].x64[fsc[sh].xcur];
+      const void* lam = adj[sh].x64[asc[sh].xcur];
+      double sr = 0.0, si = 0.0;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          int64_t e[3];
+          bool ok[3];
+          // x-edge (i, j+a, k+b), y-edge (i+a, j, k+b), z-edge (i+a, j+b, k)
+          ok[0] = (j + a < g.ny) && (k + b < g.nz);
+          e[0] = i + (int64_t)g.nx * ((j + a) + (int64_t)g.ny * (k + b));
+          ok[1] = (i + a < g.nx) && (k + b < g.nz);
+          e[1] = g.ncomp + (i + a) + (int64_t)g.nx * (j + (int64_t)g.ny * (k + b));
+          ok[2] = (i + a < g.nx) && (j + b < g.ny);
+          e[2] = 2 * g.ncomp + (i + a) + (int64_t)g.nx * ((j + b) + (int64_t)g.ny * k);
+          for (int t = 0; t < 3; ++t) {
+            if (!ok[t]) continue;
+            const C2<double> xv = ld<double>(x, e[t]);
+            const C2<double> lv = ld<double>(lam, e[t]);
+            sr += lv.re * xv.re - lv.im * xv.im;
+            si += lv.re * xv.im + lv.im * xv.re;
+          }
+        }
+      const double xr = fwd[sh].xi_re, xim = fwd[sh].xi_im;
+      acc += xr * sr - xim * si;
+    }
+    grad[cidx] = q * acc;
+  }
+}
+
+}  // namespace tem

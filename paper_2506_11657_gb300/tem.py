@@ -1,0 +1,238 @@
+"""Thin ctypes binding of the TEM C ABI (include/tem.h).
+
+Argument marshalling only: every step of the forward model, the adjoint and
+the operator runs in libtem.so's CUDA kernels.  PyTorch supplies device memory
+(through the allocator hook) and streams.  Loading fails loudly if the library
+has not been built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtem.so")
+
+TEM_OK, TEM_EINVAL, TEM_ENOMEM, TEM_ENOCONV, TEM_EBREAKDOWN, TEM_ETIMEOUT, TEM_ECUDA, TEM_EBUSY = range(8)
+PREC_FP64, PREC_MIXED = 0, 1
+
+EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
+            "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
+            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_adjoint",
+            "tem_state_destroy", "tem_apply_operator"]
+
+
+class TEMError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__(f"{what}: {status_string(code)} (code {code}) {last_error()}")
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32),
+                ("keep_state", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+
+
+def lib():
+    """Load libtem.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    L = C.CDLL(LIB_PATH)
+    L.tem_default_options.argtypes = [C.POINTER(Options)]
+    L.tem_default_options.restype = None
+    L.tem_status_string.argtypes = [C.c_int]
+    L.tem_status_string.restype = C.c_char_p
+    L.tem_last_error.argtypes = []
+    L.tem_last_error.restype = C.c_char_p
+    L.tem_version.restype = C.c_char_p
+    L.tem_build_grid.argtypes = [_dp, C.c_int64, _dp, C.c_int64, _dp, C.c_int64, _dp, _dp, C.c_void_p,
+                                 C.POINTER(C.c_void_p)]
+    L.tem_grid_set_sigma.argtypes = [C.c_void_p, _dp, C.c_void_p]
+    L.tem_grid_dims.argtypes = [C.c_void_p, _i64p]
+    L.tem_grid_destroy.argtypes = [C.c_void_p]
+    L.tem_poles_residues.argtypes = [_dp, C.c_int64, C.c_int64, _dp, _dp, _dp, _i64p, _dp]
+    L.tem_forward.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, _dp, _dp,
+                              C.c_int64, C.c_int64, C.POINTER(Options), C.c_void_p, _dp, C.POINTER(C.c_void_p)]
+    L.tem_state_stats.argtypes = [C.c_void_p, _i32p, _dp]
+    L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
+    L.tem_state_destroy.argtypes = [C.c_void_p]
+    L.tem_apply_operator.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+    _lib = L
+    return L
+
+
+def status_string(code):
+    return lib().tem_status_string(int(code)).decode()
+
+
+def last_error():
+    return lib().tem_last_error().decode()
+
+
+def _check(rc, what, ok=(TEM_OK,)):
+    if rc not in ok:
+        raise TEMError(rc, what)
+    return rc
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().tem_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+class Grid:
+    """Device-resident grid and conductivity (tem_build_grid)."""
+
+    def __init__(self, hx, hy, hz, origin, sigma, stream=None):
+        self.hx, self.hy, self.hz = _f64(hx), _f64(hy), _f64(hz)
+        self.origin = _f64(origin)
+        sig = _f64(sigma).ravel()
+        h = C.c_void_p()
+        _check(lib().tem_build_grid(_ptr(self.hx), len(self.hx), _ptr(self.hy), len(self.hy), _ptr(self.hz),
+                                    len(self.hz), _ptr(self.origin), _ptr(sig), _stream(stream), C.byref(h)),
+               "tem_build_grid")
+        self.handle = h
+
+    @property
+    def shape(self):
+        return (len(self.hx), len(self.hy), len(self.hz))
+
+    def set_sigma(self, sigma, stream=None):
+        sig = _f64(sigma).ravel()
+        _check(lib().tem_grid_set_sigma(self.handle, _ptr(sig), _stream(stream)), "tem_grid_set_sigma")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tem_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def poles_residues(t, degree, weights=None):
+    """tem_poles_residues: (shifts[s] complex, c[s, K] complex, uniform_err)."""
+    t = _f64(t)
+    K = len(t)
+    xi = np.zeros(2 * degree)
+    c = np.zeros(2 * degree * K)
+    s = C.c_int64()
+    err = C.c_double()
+    w = _f64(weights) if weights is not None else None
+    _check(lib().tem_poles_residues(_ptr(t), K, degree, _ptr(w) if w is not None else None, _ptr(xi), _ptr(c),
+                                    C.byref(s), C.byref(err)), "tem_poles_residues")
+    s = s.value
+    shifts = xi[:2 * s].view(np.complex128).copy()
+    cc = c[:2 * s * K].view(np.complex128).reshape(s, K).copy()
+    return shifts, cc, err.value
+
+
+class State:
+    """Kept shifted solutions of a forward call (for the adjoint)."""
+
+    def __init__(self, handle, s, n_rx, K, n_cells):
+        self.handle, self.s, self.n_rx, self.K, self.n_cells = handle, s, n_rx, K, n_cells
+
+    def stats(self):
+        it = np.zeros(self.s, dtype=np.int32)
+        rr = np.zeros(self.s)
+        _check(lib().tem_state_stats(self.handle, it.ctypes.data_as(_i32p), _ptr(rr)), "tem_state_stats")
+        return it, rr
+
+    def adjoint(self, dphi_dd, stream=None):
+        g = _f64(dphi_dd).reshape(self.n_rx, self.K)
+        out = np.zeros(self.n_cells)
+        rc = lib().tem_adjoint(self.handle, _ptr(g), _stream(stream), _ptr(out))
+        _check(rc, "tem_adjoint", ok=(TEM_OK, TEM_ENOCONV))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tem_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class ForwardResult:
+    d: np.ndarray
+    status: int
+    state: State | None
+
+
+def forward(grid: Grid, loop_xy, z_loop, rx, shifts, c, options: Options | None = None, current=1.0,
+            stream=None, keep_state=False) -> ForwardResult:
+    """tem_forward: d_t b_z (n_rx, K) for the given shifts and channel weights."""
+    loop = _f64(loop_xy).reshape(-1, 2)
+    rxa = _f64(rx).reshape(-1, 3)
+    shifts = np.ascontiguousarray(shifts, dtype=np.complex128)
+    cc = np.ascontiguousarray(c, dtype=np.complex128)
+    s, K = cc.shape
+    xi = shifts.view(np.float64)
+    cf = cc.view(np.float64).ravel()
+    opt = options or default_options()
+    opt.keep_state = 1 if keep_state else 0
+    out = np.zeros((len(rxa), K))
+    h = C.c_void_p()
+    rc = lib().tem_forward(grid.handle, _ptr(loop), len(loop), float(z_loop), float(current), _ptr(rxa), len(rxa),
+                           _ptr(xi), _ptr(cf), s, K, C.byref(opt), _stream(stream), _ptr(out), C.byref(h))
+    _check(rc, "tem_forward", ok=(TEM_OK, TEM_ENOCONV))
+    st = State(h, s, len(rxa), K, int(np.prod(grid.shape))) if (keep_state and h.value) else None
+    return ForwardResult(out, rc, st)
+
+
+def apply_operator(grid: Grid, shifts, p, q, precision=PREC_FP64, stream=None):
+    """q[i] = (K - xi_i M) p[i] on device tensors in the library's edge layout (see tem.h)."""
+    shifts = np.ascontiguousarray(shifts, dtype=np.complex128)
+    xi = shifts.view(np.float64)
+    _check(lib().tem_apply_operator(grid.handle, _ptr(xi), len(shifts), C.c_void_p(p.data_ptr()),
+                                    C.c_void_p(q.data_ptr()), int(precision), _stream(stream)),
+           "tem_apply_operator")
