@@ -73,12 +73,20 @@ typedef struct tem_options {
   int32_t precision;     /* TEM_PREC_FP64 (default) or TEM_PREC_MIXED */
   int32_t max_iter;      /* bound on COCG iterations per shift (default 20000) */
   double tol;            /* stop when ||f - A_i x_i||_2 <= tol ||f||_2, FP64 residual (default 1e-12) */
-  double inner_tol;      /* MIXED: relative residual reduction per FP32 inner solve (default 1e-2) */
+  double inner_tol;      /* MIXED: relative residual reduction per FP32 inner solve (default 1e-1) */
   int32_t max_outer;     /* MIXED: bound on FP64 defect-correction steps (default 40) */
   int32_t check_every;   /* iterations between host-side convergence polls (default 32) */
   int32_t keep_state;    /* nonzero: keep the solutions for tem_adjoint (state_out must be non-NULL) */
-  int32_t reserved;
+  int32_t precond;       /* TEM_PRECOND_AUTO (default), TEM_PRECOND_JACOBI or TEM_PRECOND_NODAL */
 } tem_options;
+
+/* Preconditioner of the inner COCG sweeps. */
+enum {
+  TEM_PRECOND_AUTO = 0,    /* NODAL for FP64 sweeps, JACOBI for FP32 sweeps */
+  TEM_PRECOND_JACOBI = 1,  /* z = D^{-1} r,  D = diag(K) - xi M */
+  TEM_PRECOND_NODAL = 2    /* z = D^{-1} r + G D_n^{-1} G^T r: Jacobi plus a correction in the
+                              nodal-gradient (near-null) space of K, D_n = -xi diag(G^T M G) */
+};
 
 /* Default options (see the field comments). */
 void tem_default_options(tem_options* opt);
@@ -88,6 +96,9 @@ const char* tem_status_string(int status);
 
 /* Library version string. */
 const char* tem_version(void);
+
+/* Text of the last CUDA error seen by this thread's calls (empty if none). */
+const char* tem_last_error(void);
 
 /*
  * Install the device allocator used for every buffer the library creates.
@@ -199,6 +210,29 @@ int tem_state_destroy(tem_state* state);
  */
 int tem_apply_operator(const tem_grid* grid, const double* xi, int64_t s,
                        const void* p_dev, void* q_dev, int32_t precision, void* cuda_stream);
+
+/*
+ * Number of CUDA kernels this library has launched in this process so far
+ * (monotone; for launch accounting around a timed region).
+ */
+int64_t tem_launch_count(void);
+
+/*
+ * Per-kernel timing of the solver's passes (measurement support; no paper
+ * counterpart beyond the solves of Eq. (rmj)).  Sets up the batched solve of
+ * tem_forward for `s` shifts (same loop source, precision as given), runs one
+ * FP64 residual pass and then `n_iter` COCG iterations with CUDA events around
+ * every launch on `cuda_stream`, and writes the average duration in ms of
+ *   ms_out[0] : the stencil pass  (z = D^-1 r + G psi, p <- z + beta p, q <- A p, (p, q)),
+ *   ms_out[1] : the update pass   (x += alpha p, r -= alpha q),
+ *   ms_out[2] : the FP64 residual pass,
+ *   ms_out[3] : the nodal pass    (psi = D_n^-1 G^T r, (r, z), ||r||),
+ * and units_out[0] = interior edges x shifts processed per launch.
+ * Slots that converge before n_iter stop being timed; use n_iter small enough.
+ */
+int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop,
+                       double current, const double* xi, int64_t s, int32_t precision, int32_t n_iter,
+                       void* cuda_stream, double* ms_out, double* units_out);
 
 #ifdef __cplusplus
 }

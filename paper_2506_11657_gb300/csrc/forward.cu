@@ -12,6 +12,10 @@
 #include "kernels.cuh"
 #include "solver.h"
 
+namespace tem {
+int64_t launch_count();
+}
+
 using namespace tem;
 
 struct tem_state {
@@ -41,7 +45,14 @@ int validate_poles(const double* xi, const double* c, int64_t s, int64_t K) {
   return TEM_OK;
 }
 
+int use_nodal(const tem_options& o) {
+  if (o.precond == TEM_PRECOND_NODAL) return 1;
+  if (o.precond == TEM_PRECOND_JACOBI) return 0;
+  return o.precision == TEM_PREC_FP64 ? 1 : 0;
+}
+
 int validate_options(const tem_options& o) {
+  if (o.precond < TEM_PRECOND_AUTO || o.precond > TEM_PRECOND_NODAL) return TEM_EINVAL;
   if (o.precision != TEM_PREC_FP64 && o.precision != TEM_PREC_MIXED) return TEM_EINVAL;
   if (!(o.tol > 0.0 && o.tol < 1.0)) return TEM_EINVAL;
   if (!(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return TEM_EINVAL;
@@ -56,7 +67,7 @@ int solve_shifts(const tem_grid* g, const double* xi, int s, const tem_options& 
   const int64_t ncomp = g->v.ncomp;
   const size_t per = slot_vector_bytes(ncomp, opt.precision);
   TEM_TRY(vec.alloc(per * s, st));
-  batch.reset(new Batch(opt.precision));
+  batch.reset(new Batch(opt.precision, use_nodal(opt)));
   for (int i = 0; i < s; ++i) {
     SlotVectors v = carve_slot(static_cast<char*>(vec.ptr) + per * i, ncomp, opt.precision);
     const void* rc = rhs_c_dev ? static_cast<const char*>(rhs_c_dev) + (size_t)i * 3 * ncomp * 16 : nullptr;
@@ -153,6 +164,7 @@ int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
     TEM_CUDA_TRY(cudaMemcpyAsync(d_toff, S->term_off.data(), (n_rx + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
     TEM_CUDA_TRY(cudaMemcpyAsync(d_c, c, 2 * s * K * 8, cudaMemcpyHostToDevice, st));
     k_scatter<<<(int)((fi.size() + 255) / 256 + 1), 256, 0, st>>>(d_fidx, d_fval, (int64_t)fi.size(), fbuf.as<double>());
+    count_launch();
     TEM_CUDA_TRY(cudaGetLastError());
     std::vector<double> ffs(s, ff);
     SolveStats stats;
@@ -161,6 +173,7 @@ int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
   }
   k_project_combine<<<(int)n_rx, 128, 0, st>>>(S->batch->slots_device(), S->batch->scalars_device(), int(s),
                                                  d_tedge, d_tw, d_toff, d_c, int(K), d_out, int(n_rx));
+  count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   TEM_CUDA_TRY(cudaMemcpyAsync(dbzdt_out, d_out, n_rx * K * sizeof(double), cudaMemcpyDeviceToHost, st));
   TEM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -237,6 +250,7 @@ int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) 
     TEM_CUDA_TRY(cudaMemcpyAsync(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice, st));
     TEM_CUDA_TRY(cudaMemcpyAsync(d_val, val.data(), val.size() * 8, cudaMemcpyHostToDevice, st));
     k_scatter_c<<<(int)((idx.size() + 255) / 256 + 1), 256, 0, st>>>(d_idx, d_val, (int64_t)idx.size(), rhs.as<double>());
+    count_launch();
     TEM_CUDA_TRY(cudaGetLastError());
     TEM_CUDA_TRY(cudaStreamSynchronize(st));
   }
@@ -249,6 +263,7 @@ int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) 
   k_gradient<<<152 * 8, 256, 0, st>>>(grid->v, grid->sig.as<double>(), S->batch->slots_device(),
                                        S->batch->scalars_device(), ab->slots_device(), ab->scalars_device(), s,
                                        gbuf.as<double>());
+  count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   TEM_CUDA_TRY(cudaMemcpyAsync(grad, gbuf.ptr, ncomp * sizeof(double), cudaMemcpyDeviceToHost, st));
   TEM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -282,7 +297,94 @@ int tem_apply_operator(const tem_grid* grid, const double* xi, int64_t s, const 
     k_apply<double><<<grd, NT, 0, st>>>(g, dxi.as<double>(), p_dev, q_dev, tx, ty, zchunk);
   else
     k_apply<float><<<grd, NT, 0, st>>>(g, dxi.as<double>(), p_dev, q_dev, tx, ty, zchunk);
+  count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
+  return TEM_OK;
+}
+
+int64_t tem_launch_count(void) { return tem::launch_count(); }
+
+int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop,
+                       double current, const double* xi, int64_t s, int32_t precision, int32_t n_iter,
+                       void* cuda_stream, double* ms_out, double* units_out) {
+  if (!grid || !xi || !ms_out || s < 1 || s > 64 || n_iter < 1 || n_iter > 100000) return TEM_EINVAL;
+  if (precision != TEM_PREC_FP64 && precision != TEM_PREC_MIXED) return TEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  std::vector<Term> fterms;
+  TEM_TRY(build_source(grid, loop_xy, n_vertices, z_loop, current, fterms));
+  const int64_t ncomp = grid->v.ncomp;
+  DevBuf fbuf, tbuf, vec;
+  TEM_TRY(fbuf.alloc(3 * ncomp * sizeof(double), st));
+  TEM_TRY(tbuf.alloc(fterms.size() * 16 + 256, st));
+  std::vector<int64_t> fi;
+  std::vector<double> fv;
+  double ff = 0;
+  for (auto& t : fterms) { fi.push_back(t.edge); fv.push_back(t.w); ff += t.w * t.w; }
+  int64_t* d_fidx = tbuf.as<int64_t>();
+  double* d_fval = reinterpret_cast<double*>(d_fidx + fi.size());
+  TEM_CUDA_TRY(cudaMemsetAsync(fbuf.ptr, 0, 3 * ncomp * sizeof(double), st));
+  TEM_CUDA_TRY(cudaMemcpyAsync(d_fidx, fi.data(), fi.size() * 8, cudaMemcpyHostToDevice, st));
+  TEM_CUDA_TRY(cudaMemcpyAsync(d_fval, fv.data(), fv.size() * 8, cudaMemcpyHostToDevice, st));
+  k_scatter<<<(int)((fi.size() + 255) / 256 + 1), 256, 0, st>>>(d_fidx, d_fval, (int64_t)fi.size(), fbuf.as<double>());
+  count_launch();
+  tem_options opt;
+  tem_default_options(&opt);
+  opt.precision = precision;
+  opt.tol = 1e-300;   // nothing converges during the timed iterations
+  opt.inner_tol = 1e-300;
+  const size_t per = slot_vector_bytes(ncomp, precision);
+  TEM_TRY(vec.alloc(per * s, st));
+  Batch b(precision, use_nodal(opt));
+  for (int i = 0; i < s; ++i)
+    TEM_TRY(b.add_slot(grid->v, xi[2 * i], xi[2 * i + 1], carve_slot(vec.as<char>() + per * i, ncomp, precision),
+                       fbuf.as<double>(), nullptr));
+  std::vector<double> ffs(s, ff);
+  TEM_TRY(b.setup(opt, st, ffs.data()));
+  cudaEvent_t ev[2];
+  TEM_CUDA_TRY(cudaEventCreate(&ev[0]));
+  TEM_CUDA_TRY(cudaEventCreate(&ev[1]));
+  float ms = 0;
+  TEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+  TEM_TRY(b.launch_residual(st));
+  TEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+  TEM_CUDA_TRY(cudaEventSynchronize(ev[1]));
+  TEM_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+  ms_out[2] = ms;
+  TEM_TRY(b.launch_nodal(st, 1));
+  double tot_s = 0, tot_u = 0, tot_n = 0;
+  for (int it = 0; it < n_iter; ++it) {
+    TEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+    TEM_TRY(b.launch_stencil(st));
+    TEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+    TEM_CUDA_TRY(cudaEventSynchronize(ev[1]));
+    TEM_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    tot_s += ms;
+    TEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+    TEM_TRY(b.launch_update(st));
+    TEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+    TEM_CUDA_TRY(cudaEventSynchronize(ev[1]));
+    TEM_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    tot_u += ms;
+    TEM_CUDA_TRY(cudaEventRecord(ev[0], st));
+    TEM_TRY(b.launch_nodal(st, 0));
+    TEM_CUDA_TRY(cudaEventRecord(ev[1], st));
+    TEM_CUDA_TRY(cudaEventSynchronize(ev[1]));
+    TEM_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    tot_n += ms;
+  }
+  ms_out[0] = tot_s / n_iter;
+  ms_out[1] = tot_u / n_iter;
+  ms_out[3] = tot_n / n_iter;
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (units_out) {
+    const int64_t nx = grid->v.nx, ny = grid->v.ny, nz = grid->v.nz;
+    const int64_t interior = nx * (ny - 1) * (nz - 1) + (nx - 1) * ny * (nz - 1) + (nx - 1) * (ny - 1) * nz;
+    units_out[0] = double(interior) * double(s);
+  }
+  TEM_TRY(b.fetch_scalars(st));
+  for (const auto& S : b.scalars())
+    if (S.status != TEM_OK || !S.active) return TEM_EBREAKDOWN;  // a slot stopped: the timing is not of s slots
   return TEM_OK;
 }
 

@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "tem_internal.h"
+#include "solver.h"
 
 namespace tem {
 
@@ -100,6 +101,26 @@ __global__ void k_mass(int nx, int ny, int nz, const double* hx, const double* h
   }
 }
 
+// W_n = sum over the six edges at node n of M_e / L_e^2 (interior nodes; 0 on the boundary):
+// the diagonal of G^T M G for the nodal gradient G.
+__global__ void k_node_weight(int nx, int ny, int nz, const double* hx, const double* hy, const double* hz,
+                              const double* Me, double* Wn, float* Wnf) {
+  const int64_t ncomp = (int64_t)nx * ny * nz;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ncomp; n += (int64_t)gridDim.x * blockDim.x) {
+    const int i = int(n % nx);
+    const int64_t r = n / nx;
+    const int j = int(r % ny), k = int(r / ny);
+    double w = 0.0;
+    if (i > 0 && j > 0 && k > 0) {
+      w = Me[n - 1] / (hx[i - 1] * hx[i - 1]) + Me[n] / (hx[i] * hx[i]) +
+          Me[ncomp + n - nx] / (hy[j - 1] * hy[j - 1]) + Me[ncomp + n] / (hy[j] * hy[j]) +
+          Me[2 * ncomp + n - (int64_t)nx * ny] / (hz[k - 1] * hz[k - 1]) + Me[2 * ncomp + n] / (hz[k] * hz[k]);
+    }
+    Wn[n] = w;
+    Wnf[n] = float(w);
+  }
+}
+
 static bool finite_positive(const double* a, int64_t n) {
   for (int64_t q = 0; q < n; ++q)
     if (!(std::isfinite(a[q]) && a[q] > 0.0)) return false;
@@ -131,13 +152,21 @@ static int upload_sigma(tem_grid* g, const double* sigma, cudaStream_t st) {
   if (!sigma || !finite_positive(sigma, ncell)) return TEM_EINVAL;
   g->sigma.assign(sigma, sigma + ncell);
   TEM_CUDA_TRY(cudaMemcpyAsync(g->sig.ptr, sigma, ncell * sizeof(double), cudaMemcpyHostToDevice, st));
+  // layout: Me (3n doubles), Wn (n doubles), Mef (3n floats), Wnf (n floats) -- every block aligned
   double* Me = g->me.as<double>();
-  float* Mef = reinterpret_cast<float*>(Me + 3 * ncell);
+  double* Wn = Me + 3 * ncell;
+  float* Mef = reinterpret_cast<float*>(Wn + ncell);
+  float* Wnf = Mef + 3 * ncell;
   const double* geo = g->geo.as<double>();
   const int nx = g->v.nx, ny = g->v.ny, nz = g->v.nz;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((3 * ncell + threads - 1) / threads, 152 * 32);
   k_mass<<<(int)blocks, threads, 0, st>>>(nx, ny, nz, geo, geo + nx, geo + nx + ny, g->sig.as<double>(), Me, Mef);
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
+  k_node_weight<<<(int)std::min<int64_t>((ncell + threads - 1) / threads, 152 * 32), threads, 0, st>>>(
+      nx, ny, nz, geo, geo + nx, geo + nx + ny, Me, Wn, Wnf);
+  count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
 }
@@ -176,7 +205,7 @@ void tem_default_options(tem_options* opt) {
   opt->precision = TEM_PREC_FP64;
   opt->max_iter = 20000;
   opt->tol = 1e-12;
-  opt->inner_tol = 1e-2;
+  opt->inner_tol = 1e-1;
   opt->max_outer = 40;
   opt->check_every = 32;
   opt->keep_state = 0;
@@ -218,7 +247,7 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   put(nx + ny, g->hz);
   for (int64_t q = 0; q < 6 * n1; ++q) geof[q] = float(geo[q]);
   int rc = g->geo.alloc(6 * n1 * (sizeof(double) + sizeof(float)), st);
-  if (rc == TEM_OK) rc = g->me.alloc(3 * ncell * (sizeof(double) + sizeof(float)), st);
+  if (rc == TEM_OK) rc = g->me.alloc(4 * ncell * (sizeof(double) + sizeof(float)), st);
   if (rc == TEM_OK) rc = g->sig.alloc(ncell * sizeof(double), st);
   if (rc != TEM_OK) {
     delete g;
@@ -242,7 +271,9 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   v.Lxf = gf; v.Lyf = gf + nx; v.Lzf = gf + nx + ny;
   v.Sxf = gf + 3 * n1; v.Syf = gf + 3 * n1 + nx; v.Szf = gf + 3 * n1 + nx + ny;
   v.Me = g->me.as<double>();
-  v.Mef = reinterpret_cast<const float*>(v.Me + 3 * ncell);
+  v.Wn = v.Me + 3 * ncell;
+  v.Mef = reinterpret_cast<const float*>(v.Wn + ncell);
+  v.Wnf = v.Mef + 3 * ncell;
   rc = upload_sigma(g, sigma, st);
   if (rc == TEM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = TEM_ECUDA;
   if (rc != TEM_OK) {

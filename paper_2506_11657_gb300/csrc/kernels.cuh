@@ -63,10 +63,12 @@ template <class T> struct Geo;
 template <> struct Geo<double> {
   const double *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Me;
   __device__ Geo(const GridView& g) : Lx(g.Lx), Ly(g.Ly), Lz(g.Lz), Sx(g.Sx), Sy(g.Sy), Sz(g.Sz), Me(g.Me) {}
+  __device__ static const double* Wn(const GridView& g) { return g.Wn; }
 };
 template <> struct Geo<float> {
   const float *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Me;
   __device__ Geo(const GridView& g) : Lx(g.Lxf), Ly(g.Lyf), Lz(g.Lzf), Sx(g.Sxf), Sy(g.Syf), Sz(g.Szf), Me(g.Mef) {}
+  __device__ static const float* Wn(const GridView& g) { return g.Wnf; }
 };
 
 // Diagonal of K at edge (c, i, j, k) (valid, non-boundary edges only):
@@ -168,7 +170,7 @@ __device__ __forceinline__ void load_plane(StencilSmem<T>& sm, int b, int k, int
     if (k >= 0 && k < g.nz && i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
       const int64_t idx = (int64_t)c * g.ncomp + i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
       const bool own = own_plane && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY;
-      v = pol.load(idx, own);
+      v = pol.load(c, i, j, k, idx, own);
     }
     sm.P[b][c][jj][ii] = v;
   }
@@ -274,11 +276,12 @@ __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView
 struct BatchArgs {
   const SlotDesc* slots;
   SlotScalars* sc;
-  const int* blk2slot;       // stencil launch: CTA -> slot
+  const int* blk2slot;       // stencil / residual launch: CTA -> slot
   const int* ublk2slot;      // update launch: CTA -> slot
-  double* part;              // [slot][maxblk][4]
+  const int* nblk2slot;      // nodal launch: CTA -> slot
+  double* part;              // [slot][part_stride] partial sums
   unsigned* ticket;          // [slot]
-  int* n_active;             // slots still iterating
+  int* n_active;             // slots armed or iterating
   int part_stride;           // doubles per slot in part
   int zchunk;                // planes per stencil CTA
 };
@@ -295,22 +298,59 @@ __device__ __forceinline__ void tile_of(const SlotDesc& d, int lb, int zchunk, i
   k1 = min(k0 + zchunk, nz);
 }
 
-// ---------------------------------------------------- pass 1: p <- z + beta p; q <- A p
+// ---------------------------------------------------------- the preconditioner
+// Jacobi on the edges plus a nodal correction in the gradient (near-null) space of K
+// (the auxiliary-space idea of Hiptmair & Xu 2007):
+//     z = D^{-1} r + G psi,   psi = D_n^{-1} G^T r,
+//     D = diag(K) - xi M,     D_n = diag(G^T A G) = -xi diag(G^T M G) = -xi W,
+// with G the nodal gradient ((G phi)_e = (phi_end - phi_start) / L_e) on interior
+// nodes.  Both terms are complex symmetric, so COCG applies.
+template <class T>
+__device__ __forceinline__ C2<T> jacobi_D(const Geo<T>& G, int c, int i, int j, int k, int64_t idx, C2<T> xi) {
+  return C2<T>(diagK<T>(G, c, i, j, k), T(0)) - (G.Me[idx] * xi);
+}
+
+template <class T>
+__device__ __forceinline__ C2<T> precond_z(const Geo<T>& G, const GridView& g, int c, int i, int j, int k,
+                                           int64_t idx, C2<T> rv, C2<T> xi, const void* psi) {
+  C2<T> z = cdiv(rv, jacobi_D<T>(G, c, i, j, k, idx, xi));
+  if (!psi) return z;
+  const int64_t n0 = i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+  const C2<T> ps = ld<T>(psi, n0);
+  C2<T> pe = czero<T>();
+  T rl;
+  if (c == 0) {
+    if (i + 1 < g.nx) pe = ld<T>(psi, n0 + 1);
+    rl = T(1) / G.Lx[i];
+  } else if (c == 1) {
+    if (j + 1 < g.ny) pe = ld<T>(psi, n0 + g.nx);
+    rl = T(1) / G.Ly[j];
+  } else {
+    if (k + 1 < g.nz) pe = ld<T>(psi, n0 + (int64_t)g.nx * g.ny);
+    rl = T(1) / G.Lz[k];
+  }
+  return z + rl * (pe - ps);
+}
+
+// ------------------------------------- pass A: p <- z + beta p; q <- A p; (p, q) -> alpha
 template <class T>
 struct CocgStencilPol {
-  const void* z; const void* pold; void* pnew; void* q;
+  const void* r; const void* psi; const void* pold; void* pnew; void* q;
   C2<T> beta; bool use_beta;
   C2<T> xi;
-  const T* Me;
+  Geo<T> G;
+  const GridView* g;
   C2<T> acc;
-  __device__ C2<T> load(int64_t idx, bool own) {
-    C2<T> v = ld<T>(z, idx);
+  __device__ CocgStencilPol(const GridView& gv) : G(gv), g(&gv) {}
+  __device__ C2<T> load(int c, int i, int j, int k, int64_t idx, bool own) {
+    if (!edge_valid(c, i, j, k)) return czero<T>();  // boundary: p stays 0 (buffers start zeroed)
+    C2<T> v = precond_z<T>(G, *g, c, i, j, k, idx, ld<T>(r, idx), xi, psi);
     if (use_beta) v = v + cmul(beta, ld<T>(pold, idx));
     if (own) st<T>(pnew, idx, v);
     return v;
   }
   __device__ void edge(int, int64_t idx, int, int, int, C2<T> p, C2<T> kp) {
-    const C2<T> qv = kp - cmul(xi, Me[idx] * p);
+    const C2<T> qv = kp - cmul(xi, G.Me[idx] * p);
     st<T>(q, idx, qv);
     acc = acc + cmul(p, qv);
   }
@@ -327,15 +367,15 @@ __global__ void __launch_bounds__(NT) k_cocg_stencil(BatchArgs A) {
   const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
   tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
-  CocgStencilPol<T> pol;
-  pol.z = d.z;
+  CocgStencilPol<T> pol(d.g);
+  pol.r = d.r;
+  pol.psi = d.nodal ? d.psi : nullptr;
   pol.pold = S->parity ? d.p1 : d.p0;
   pol.pnew = S->parity ? d.p0 : d.p1;
   pol.q = d.q;
   pol.beta = C2<T>(T(S->beta_re), T(S->beta_im));
   pol.use_beta = !(S->beta_re == 0.0 && S->beta_im == 0.0);
   pol.xi = C2<T>(T(d.xi_re), T(d.xi_im));
-  pol.Me = Geo<T>(d.g).Me;
   pol.acc = czero<T>();
   stencil_march<T>(sm, d.g, pol, i0, j0, k0, k1);
   double v[2] = {double(pol.acc.re), double(pol.acc.im)};
@@ -350,6 +390,7 @@ __global__ void __launch_bounds__(NT) k_cocg_stencil(BatchArgs A) {
     if (!(den > 0.0) || !isfinite(den)) {
       S->status = TEM_EBREAKDOWN;
       S->active = 0;
+      S->total_iters += S->iters;
       atomicSub(A.n_active, 1);
     } else {
       S->alpha_re = (S->rho_re * tot[0] + S->rho_im * tot[1]) / den;
@@ -358,59 +399,97 @@ __global__ void __launch_bounds__(NT) k_cocg_stencil(BatchArgs A) {
   }
 }
 
-// ------------------------------------- pass 2: x += alpha p; r -= alpha q; z = r / D
-// r itself is not stored: r = D z is rebuilt from the stored preconditioned residual.
+// ------------------------------------------------- pass B: x += alpha p; r -= alpha q
+// A pure stream over the slot's entries: boundary entries hold p = q = 0 and stay put.
 template <class T>
 __global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
-  __shared__ double red[NT / 32 * 4];
   const int slot = A.ublk2slot[blockIdx.x];
-  SlotScalars* S = A.sc + slot;
+  const SlotScalars* S = A.sc + slot;
   if (!S->active) return;
-  const SlotDesc d = A.slots[slot];
+  const SlotDesc& d = A.slots[slot];
   const int lb = blockIdx.x - d.blk_update0;
+  const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
+  const bool first = d.x_fresh && S->iters == 0;  // MIXED: the correction starts at 0
+  const void* p = S->parity ? d.p0 : d.p1;         // the direction written by pass A
+  void* x = d.x;
+  void* r = d.r;
+  const void* q = d.q;
+  const int64_t n = 3 * d.g.ncomp;
+  const int64_t per = (n + d.nblk_update - 1) / d.nblk_update;
+  const int64_t e0 = (int64_t)lb * per, e1 = min(n, e0 + per);
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += NT) {
+    const C2<T> pv = ld<T>(p, e);
+    C2<T> xv = cmul(alpha, pv);
+    if (!first) xv = xv + ld<T>(x, e);
+    st<T>(x, e, xv);
+    st<T>(r, e, ld<T>(r, e) - cmul(alpha, ld<T>(q, e)));
+  }
+}
+
+// --------------------- pass C: psi = D_n^{-1} G^T r;  rho = (r, z);  ||r||^2 -> beta, stop
+// Each node owns the three edges that leave it, so the edge part of (r, z) = r^T D^{-1} r
+// and ||r||^2 are summed once; (r, G psi) = (G^T r, psi) is the nodal part.
+template <class T>
+__global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A, int init_only) {
+  __shared__ double red[NT / 32 * 4];
+  const int slot = A.nblk2slot[blockIdx.x];
+  SlotScalars* S = A.sc + slot;
+  const bool pend = S->pending != 0;
+  if (!(pend || (S->active && !init_only))) return;
+  const SlotDesc& d = A.slots[slot];
   const GridView& g = d.g;
   const Geo<T> G(g);
-  const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
+  const int lb = blockIdx.x - d.blk_nodal0;
   const C2<T> xi(T(d.xi_re), T(d.xi_im));
-  const bool first = d.x_fresh && S->iters == 0;  // MIXED: the correction starts at 0
-  const void* p = S->parity ? d.p0 : d.p1;  // the direction written by pass 1
-  C2<T> rz = czero<T>();
+  const T* Wn = Geo<T>::Wn(g);
+  const uint32_t nn = (uint32_t)g.ncomp;
+  const uint32_t per = (nn + d.nblk_nodal - 1) / d.nblk_nodal;
+  const uint32_t n0 = (uint32_t)lb * per, n1 = min(nn, n0 + per);
+  const int64_t nc = g.ncomp;
+  const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+  C2<T> rho = czero<T>();
   T rr = T(0);
-  // each CTA owns a contiguous range of entries of the slot; entry e = row * nx + i with
-  // row = c * ny * nz + k * ny + j
-  const uint32_t n = (uint32_t)(3 * g.ncomp);
-  const uint32_t per = (n + d.nblk_update - 1) / d.nblk_update;
-  const uint32_t e0 = (uint32_t)lb * per, e1 = min(n, e0 + per);
-  for (uint32_t e = e0 + threadIdx.x; e < e1; e += NT) {
-    const uint32_t row = fdiv(e, d.div_nx);
-    const int i = int(e - row * (uint32_t)g.nx);
-    const uint32_t c = fdiv(row, d.div_nynz);
-    const uint32_t jk = row - c * (uint32_t)(g.ny * g.nz);
-    const uint32_t k = fdiv(jk, d.div_ny);
-    const int j = int(jk - k * (uint32_t)g.ny);
-    if (!edge_valid(int(c), i, j, int(k))) continue;
-    const C2<T> D = C2<T>(diagK<T>(G, int(c), i, j, int(k)), T(0)) - (G.Me[e] * xi);
-    const C2<T> pv = ld<T>(p, e);
-    const C2<T> qv = ld<T>(d.q, e);
-    C2<T> r = cmul(D, ld<T>(d.z, e));
-    r = r - cmul(alpha, qv);
-    C2<T> xv = cmul(alpha, pv);
-    if (!first) xv = xv + ld<T>(d.x, e);
-    st<T>(d.x, e, xv);
-    const C2<T> zv = cdiv(r, D);
-    st<T>(d.z, e, zv);
-    rz = rz + cmul(r, zv);
-    rr += r.re * r.re + r.im * r.im;
+  for (uint32_t n = n0 + threadIdx.x; n < n1; n += NT) {
+    const uint32_t row = fdiv(n, d.div_nx);
+    const int i = int(n - row * (uint32_t)g.nx);
+    const uint32_t k = fdiv(row, d.div_ny);
+    const int j = int(row - k * (uint32_t)g.ny);
+    // own edges
+    const C2<T> rx = ld<T>(d.r, n), ry = ld<T>(d.r, nc + n), rz = ld<T>(d.r, 2 * nc + n);
+    if (edge_valid(0, i, j, int(k))) rho = rho + cmul(rx, cdiv(rx, jacobi_D<T>(G, 0, i, j, int(k), n, xi)));
+    if (edge_valid(1, i, j, int(k))) rho = rho + cmul(ry, cdiv(ry, jacobi_D<T>(G, 1, i, j, int(k), nc + n, xi)));
+    if (edge_valid(2, i, j, int(k))) rho = rho + cmul(rz, cdiv(rz, jacobi_D<T>(G, 2, i, j, int(k), 2 * nc + n, xi)));
+    rr += rx.re * rx.re + rx.im * rx.im + ry.re * ry.re + ry.im * ry.im + rz.re * rz.re + rz.im * rz.im;
+    C2<T> ps = czero<T>();
+    if (d.nodal && i > 0 && j > 0 && k > 0) {
+      // (G^T r)_n = sum over the 6 edges at n of (+1 if n ends the edge, -1 if it starts it) r_e / L_e
+      const C2<T> div = (T(1) / G.Lx[i - 1]) * ld<T>(d.r, n - 1) - (T(1) / G.Lx[i]) * rx +
+                        (T(1) / G.Ly[j - 1]) * ld<T>(d.r, nc + n - sy) - (T(1) / G.Ly[j]) * ry +
+                        (T(1) / G.Lz[k - 1]) * ld<T>(d.r, 2 * nc + n - sz) - (T(1) / G.Lz[k]) * rz;
+      const C2<T> Dn = Wn[n] * C2<T>(-xi.re, -xi.im);
+      ps = cdiv(div, Dn);
+      rho = rho + cmul(div, ps);
+    }
+    if (d.nodal) st<T>(d.psi, n, ps);
   }
-  double v[3] = {double(rz.re), double(rz.im), double(rr)};
+  double v[3] = {double(rho.re), double(rho.im), double(rr)};
   block_sum<3, NT>(v, red);
   double* part = A.part + (int64_t)slot * A.part_stride;
-  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_update, lb)) {
+  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_nodal, lb)) {
     double tot[3];
-    sum_partials<3, NT>(part, d.nblk_update, tot, red);
+    sum_partials<3, NT>(part, d.nblk_nodal, tot, red);
     if (threadIdx.x != 0) return;
-    S->iters += 1;
     S->rr = tot[2];
+    if (pend) {  // first nodal pass of an inner solve: rho_0, beta = 0
+      S->pending = 0;
+      S->rho_re = tot[0];
+      S->rho_im = tot[1];
+      S->beta_re = 0.0;
+      S->beta_im = 0.0;
+      S->active = 1;
+      return;
+    }
+    S->iters += 1;
     bool done = false;
     if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
       S->status = TEM_EBREAKDOWN;
@@ -441,21 +520,18 @@ __global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
   }
 }
 
-
 // ------------------------------- FP64 residual pass (the outer defect-correction step)
 // x <- x64[cur] (+ inv_scale_prev * delta for MIXED, written to x64[cur^1]);
-// r = b - A x in FP64;  z_inner = (scale r) / D  in the inner precision TI;
+// r = b - A x in FP64;  r_inner = scale * r in the inner precision TI;
 // then (last CTA) either finish the slot or arm the next inner COCG solve.
 template <class TI>
 struct ResidualPol {
   const void* xcur; const void* delta; void* xnext; double inv_sc; bool upd;
   const double* f; const void* rhs_c;
   C2<double> xi; const double* Me;
-  Geo<TI> GI; TI xi_re_i, xi_im_i;
-  void* z; double scale;
-  double rr, rz_re, rz_im;
-  __device__ ResidualPol(const GridView& g) : GI(g) {}
-  __device__ C2<double> load(int64_t idx, bool own) {
+  void* rin; double scale;
+  double rr;
+  __device__ C2<double> load(int, int, int, int, int64_t idx, bool own) {
     C2<double> x = ld<double>(xcur, idx);
     if (upd) {
       const C2<TI> dv = ld<TI>(delta, idx);
@@ -464,20 +540,14 @@ struct ResidualPol {
     }
     return x;
   }
-  __device__ void edge(int c, int64_t idx, int i, int j, int k, C2<double> xv, C2<double> kx) {
+  __device__ void edge(int, int64_t idx, int, int, int, C2<double> xv, C2<double> kx) {
     const C2<double> ax = kx - cmul(xi, Me[idx] * xv);
     const C2<double> b = rhs_c ? ld<double>(rhs_c, idx) : C2<double>(f[idx], 0.0);
     const C2<double> r = b - ax;
     rr += r.re * r.re + r.im * r.im;
-    const C2<TI> rs(TI(scale * r.re), TI(scale * r.im));
-    const C2<TI> D = C2<TI>(diagK<TI>(GI, c, i, j, k), TI(0)) - (GI.Me[idx] * C2<TI>(xi_re_i, xi_im_i));
-    const C2<TI> zv = cdiv(rs, D);
-    st<TI>(z, idx, zv);
-    const C2<TI> p = cmul(rs, zv);
-    rz_re += double(p.re);
-    rz_im += double(p.im);
+    st<TI>(rin, idx, C2<TI>(TI(scale * r.re), TI(scale * r.im)));
   }
-  __device__ void edge_invalid(int64_t idx) { st<TI>(z, idx, czero<TI>()); }
+  __device__ void edge_invalid(int64_t idx) { st<TI>(rin, idx, czero<TI>()); }
 };
 
 template <class TI>
@@ -485,12 +555,12 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
   __shared__ StencilSmem<double> sm;
   const int slot = A.blk2slot[blockIdx.x];
   SlotScalars* S = A.sc + slot;
-  if (S->done || S->active) return;  // finished, or its inner solve is still running
+  if (S->done || S->active || S->pending) return;  // finished, or an inner solve is under way
   const SlotDesc d = A.slots[slot];
   const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
   tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
-  ResidualPol<TI> pol(d.g);
+  ResidualPol<TI> pol;
   pol.upd = d.x_fresh && S->outer > 0;
   pol.xcur = d.x64[S->xcur];
   pol.xnext = d.x64[S->xcur ^ 1];
@@ -500,24 +570,22 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
   pol.rhs_c = d.rhs_c;
   pol.xi = C2<double>(d.xi_re, d.xi_im);
   pol.Me = d.g.Me;
-  pol.xi_re_i = TI(d.xi_re);
-  pol.xi_im_i = TI(d.xi_im);
-  pol.z = d.z;
+  pol.rin = d.r;
   pol.scale = S->scale;
-  pol.rr = pol.rz_re = pol.rz_im = 0.0;
+  pol.rr = 0.0;
   stencil_march<double>(sm, d.g, pol, i0, j0, k0, k1);
-  double v[3] = {pol.rr, pol.rz_re, pol.rz_im};
-  block_sum<3, NT>(v, sm.red);
+  double v[1] = {pol.rr};
+  block_sum<1, NT>(v, sm.red);
   double* part = A.part + (int64_t)slot * A.part_stride;
-  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_stencil, lb)) {
-    double tot[3];
-    sum_partials<3, NT>(part, d.nblk_stencil, tot, sm.red);
+  if (publish_partial<1>(v, part, A.ticket + slot, d.nblk_stencil, lb)) {
+    double tot[1];
+    sum_partials<1, NT>(part, d.nblk_stencil, tot, sm.red);
     if (threadIdx.x != 0) return;
     if (pol.upd) S->xcur ^= 1;
     S->rr64 = tot[0];
     S->outer += 1;
     bool finish = false;
-    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
+    if (!isfinite(tot[0])) {
       S->status = TEM_EBREAKDOWN;
       finish = true;
     } else if (tot[0] <= S->tol_outer2) {
@@ -533,21 +601,18 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
       atomicAdd(n_done, 1);
       return;
     }
-    // arm the inner solve on  A delta = scale * r  (MIXED)  or continue x (FP64)
+    // arm the inner solve on  A delta = scale * r  (MIXED)  or continue x (FP64);
+    // the nodal pass computes rho_0 and starts it
     const double sc = S->scale;
     S->bb = sc * sc * tot[0];
     const double want = 0.25 * S->tol_outer2 / tot[0];   // reach 1/2 of the final target
     const double rel2 = d.x_fresh ? fmax(S->inner_rel2, want) : want;
     S->tol2 = rel2 * S->bb;
-    S->rho_re = tot[1];
-    S->rho_im = tot[2];
-    S->beta_re = 0.0;
-    S->beta_im = 0.0;
     S->iters = 0;
     S->parity = 0;
     S->inv_scale_prev = 1.0 / sc;
     if (d.x_fresh) S->scale = 1.0 / sqrt(tot[0]);
-    S->active = 1;
+    S->pending = 1;
     atomicAdd(A.n_active, 1);
   }
 }
@@ -556,7 +621,7 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
 template <class T>
 struct ApplyPol {
   const void* p; void* q; C2<T> xi; const T* Me;
-  __device__ C2<T> load(int64_t idx, bool) { return ld<T>(p, idx); }
+  __device__ C2<T> load(int, int, int, int, int64_t idx, bool) { return ld<T>(p, idx); }
   __device__ void edge(int, int64_t idx, int, int, int, C2<T> pv, C2<T> kp) {
     st<T>(q, idx, kp - cmul(xi, Me[idx] * pv));
   }

@@ -9,6 +9,7 @@
 //               relative reduction inner_tol; the next outer step adds d / s
 //               to x in FP64 and recomputes r in FP64 (defect correction).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "kernels.cuh"
@@ -16,14 +17,18 @@
 
 namespace tem {
 
+static std::atomic<int64_t> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+int64_t launch_count() { return g_launches.load(); }
+
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 size_t slot_vector_bytes(int64_t ncomp, int precision) {
   const size_t n = 3 * (size_t)ncomp;
-  const size_t v64 = align256(n * 16);
-  if (precision == TEM_PREC_FP64) return 5 * v64;  // x64, z, p0, p1, q
-  const size_t v32 = align256(n * 8);
-  return 2 * v64 + 5 * v32;                        // x64[2], d, z, p0, p1, q
+  const size_t v64 = align256(n * 16), n64 = align256((size_t)ncomp * 16);
+  if (precision == TEM_PREC_FP64) return 5 * v64 + n64;  // x64, r, p0, p1, q; psi
+  const size_t v32 = align256(n * 8), n32 = align256((size_t)ncomp * 8);
+  return 2 * v64 + 5 * v32 + n32;                        // x64[2], d, r, p0, p1, q; psi
 }
 
 SlotVectors carve_slot(void* base, int64_t ncomp, int precision) {
@@ -34,12 +39,14 @@ SlotVectors carve_slot(void* base, int64_t ncomp, int precision) {
   if (precision == TEM_PREC_FP64) {
     v.x64[0] = b; v.x64[1] = b;
     v.inner_x = b;
-    v.z = b + v64; v.p0 = b + 2 * v64; v.p1 = b + 3 * v64; v.q = b + 4 * v64;
+    v.r = b + v64; v.p0 = b + 2 * v64; v.p1 = b + 3 * v64; v.q = b + 4 * v64;
+    v.psi = b + 5 * v64;
   } else {
     const size_t v32 = align256(n * 8);
     v.x64[0] = b; v.x64[1] = b + v64;
     char* c = b + 2 * v64;
-    v.inner_x = c; v.z = c + v32; v.p0 = c + 2 * v32; v.p1 = c + 3 * v32; v.q = c + 4 * v32;
+    v.inner_x = c; v.r = c + v32; v.p0 = c + 2 * v32; v.p1 = c + 3 * v32; v.q = c + 4 * v32;
+    v.psi = c + 5 * v32;
   }
   return v;
 }
@@ -57,7 +64,8 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
   d.xi_re = xi_re;
   d.xi_im = xi_im;
   d.x = v.inner_x;
-  d.z = v.z;
+  d.r = v.r;
+  d.psi = v.psi;
   d.p0 = v.p0;
   d.p1 = v.p1;
   d.q = v.q;
@@ -66,6 +74,7 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
   d.f = f_real;
   d.rhs_c = static_cast<const double*>(rhs_complex);
   d.x_fresh = precision_ == TEM_PREC_MIXED ? 1 : 0;
+  d.nodal = nodal_;
   d.div_nx = make_fastdiv((uint32_t)g.nx);
   d.div_ny = make_fastdiv((uint32_t)g.ny);
   d.div_nynz = make_fastdiv((uint32_t)(g.ny * g.nz));
@@ -77,28 +86,33 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
   const int ns = (int)slots_h_.size();
   if (ns == 0) return TEM_EINVAL;
   // decomposition
-  int blk_s = 0, blk_u = 0, max_part = 0;
+  int blk_s = 0, blk_u = 0, blk_n = 0, max_part = 0;
   for (auto& d : slots_h_) {
     d.tiles_x = (d.g.nx + TX - 1) / TX;
     d.tiles_y = (d.g.ny + TY - 1) / TY;
     d.zchunks = (d.g.nz + zchunk_ - 1) / zchunk_;
     d.nblk_stencil = d.tiles_x * d.tiles_y * d.zchunks;
     const int64_t n = 3 * d.g.ncomp;
-    d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (n + NT * 16 - 1) / (NT * 16)));
+    d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + NT * 8 - 1) / (NT * 8)));
+    d.nblk_nodal = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (d.g.ncomp + NT * 8 - 1) / (NT * 8)));
     d.blk_stencil0 = blk_s;
     d.blk_update0 = blk_u;
+    d.blk_nodal0 = blk_n;
     blk_s += d.nblk_stencil;
     blk_u += d.nblk_update;
-    max_part = std::max(max_part, std::max(d.nblk_stencil, d.nblk_update) * 4);
+    blk_n += d.nblk_nodal;
+    max_part = std::max(max_part, std::max(d.nblk_stencil, d.nblk_nodal) * 4);
   }
   nblk_stencil_ = blk_s;
   nblk_update_ = blk_u;
+  nblk_nodal_ = blk_n;
   part_stride_ = max_part;
-  std::vector<int> map(blk_s + blk_u);
+  std::vector<int> map(blk_s + blk_u + blk_n);
   for (int q = 0; q < ns; ++q) {
     const SlotDesc& d = slots_h_[q];
     for (int b = 0; b < d.nblk_stencil; ++b) map[d.blk_stencil0 + b] = q;
     for (int b = 0; b < d.nblk_update; ++b) map[blk_s + d.blk_update0 + b] = q;
+    for (int b = 0; b < d.nblk_nodal; ++b) map[blk_s + blk_u + d.blk_nodal0 + b] = q;
   }
   sc_h_.assign(ns, SlotScalars());
   for (int q = 0; q < ns; ++q) {
@@ -131,19 +145,21 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
     const size_t es = precision_ == TEM_PREC_FP64 ? 16 : 8;
     TEM_CUDA_TRY(cudaMemsetAsync(d.p0, 0, n * es, st));
     TEM_CUDA_TRY(cudaMemsetAsync(d.p1, 0, n * es, st));
+    TEM_CUDA_TRY(cudaMemsetAsync(d.psi, 0, (size_t)d.g.ncomp * es, st));
     if (d.x != d.x64[0]) TEM_CUDA_TRY(cudaMemsetAsync(d.x, 0, n * es, st));
   }
   if (!counters_h_) TEM_CUDA_TRY(cudaHostAlloc(&counters_h_, 2 * sizeof(int), cudaHostAllocDefault));
   return TEM_OK;
 }
 
-static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& map, int nblk_s,
+static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& map, int nblk_s, int nblk_u,
                            const DevBuf& part, const DevBuf& ticket, const DevBuf& counters, int stride, int zchunk) {
   BatchArgs A;
   A.slots = slots.as<SlotDesc>();
   A.sc = sc.as<SlotScalars>();
   A.blk2slot = map.as<int>();
   A.ublk2slot = map.as<int>() + nblk_s;
+  A.nblk2slot = map.as<int>() + nblk_s + nblk_u;
   A.part = part.as<double>();
   A.ticket = ticket.as<unsigned>();
   A.n_active = counters.as<int>();
@@ -152,26 +168,53 @@ static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& 
   return A;
 }
 
-int Batch::launch_iteration(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
-  if (precision_ == TEM_PREC_FP64) {
+int Batch::launch_stencil(cudaStream_t st) {
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  if (precision_ == TEM_PREC_FP64)
     k_cocg_stencil<double><<<nblk_stencil_, NT, 0, st>>>(A);
-    k_cocg_update<double><<<nblk_update_, NT, 0, st>>>(A);
-  } else {
+  else
     k_cocg_stencil<float><<<nblk_stencil_, NT, 0, st>>>(A);
-    k_cocg_update<float><<<nblk_update_, NT, 0, st>>>(A);
-  }
+  count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
 }
 
+int Batch::launch_update(cudaStream_t st) {
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  if (precision_ == TEM_PREC_FP64)
+    k_cocg_update<double><<<nblk_update_, NT, 0, st>>>(A);
+  else
+    k_cocg_update<float><<<nblk_update_, NT, 0, st>>>(A);
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
+  return TEM_OK;
+}
+
+int Batch::launch_nodal(cudaStream_t st, int init_only) {
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  if (precision_ == TEM_PREC_FP64)
+    k_cocg_nodal<double><<<nblk_nodal_, NT, 0, st>>>(A, init_only);
+  else
+    k_cocg_nodal<float><<<nblk_nodal_, NT, 0, st>>>(A, init_only);
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
+  return TEM_OK;
+}
+
+int Batch::launch_iteration(cudaStream_t st) {
+  TEM_TRY(launch_stencil(st));
+  TEM_TRY(launch_update(st));
+  return launch_nodal(st, 0);
+}
+
 int Batch::launch_residual(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
   int* n_done = counters_d_.as<int>() + 1;
   if (precision_ == TEM_PREC_FP64)
     k_residual<double><<<nblk_stencil_, NT, 0, st>>>(A, n_done);
   else
     k_residual<float><<<nblk_stencil_, NT, 0, st>>>(A, n_done);
+  count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
 }
@@ -189,7 +232,8 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
     return TEM_OK;
   };
   TEM_TRY(launch_residual(st));
-  ++launches;
+  TEM_TRY(launch_nodal(st, 1));
+  launches += 2;
   TEM_TRY(poll());
   int64_t rounds = 0;
   while (counters_h_[1] < ns) {
@@ -197,12 +241,14 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
     if (counters_h_[0] > 0) {
       for (int it = 0; it < every; ++it) {
         TEM_TRY(launch_iteration(st));
-        launches += 2;
+        launches += 3;
       }
     }
-    // slots whose inner solve ended take their FP64 outer step; the others skip it
+    // slots whose inner solve ended take their FP64 outer step (the others skip it),
+    // and the nodal pass starts the inner solves that step armed
     TEM_TRY(launch_residual(st));
-    ++launches;
+    TEM_TRY(launch_nodal(st, 1));
+    launches += 2;
     TEM_TRY(poll());
   }
   TEM_TRY(fetch_scalars(st));

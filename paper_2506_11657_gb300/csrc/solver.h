@@ -9,7 +9,8 @@ namespace tem {
 struct SlotVectors {
   void* x64[2];
   void* inner_x;   // MIXED: FP32 correction; FP64: == x64[0]
-  void* z;
+  void* r;
+  void* psi;
   void* p0;
   void* p1;
   void* q;
@@ -28,7 +29,7 @@ struct SolveStats {
 class Batch {
  public:
   // Slots must be added before setup(); all share one precision.
-  explicit Batch(int precision) : precision_(precision) {}
+  Batch(int precision, int nodal) : precision_(precision), nodal_(nodal) {}
   ~Batch();
   int add_slot(const GridView& g, double xi_re, double xi_im, const SlotVectors& v,
                const double* f_real, const void* rhs_complex);
@@ -45,19 +46,27 @@ class Batch {
   int zchunk() const { return zchunk_; }
   int stencil_blocks() const { return nblk_stencil_; }
   int update_blocks() const { return nblk_update_; }
+  int nodal_blocks() const { return nblk_nodal_; }
   // launch one (stencil, update) pair or one residual pass for all slots (bench / profiling)
   int launch_iteration(cudaStream_t st);
+  int launch_stencil(cudaStream_t st);
+  int launch_update(cudaStream_t st);
+  int launch_nodal(cudaStream_t st, int init_only);
   int launch_residual(cudaStream_t st);
 
  private:
   int precision_;
+  int nodal_;
   int zchunk_ = 32;
   std::vector<SlotDesc> slots_h_;
   std::vector<SlotScalars> sc_h_;
-  int nblk_stencil_ = 0, nblk_update_ = 0;
+  int nblk_stencil_ = 0, nblk_update_ = 0, nblk_nodal_ = 0;
   int part_stride_ = 0;
   DevBuf slots_d_, sc_d_, map_d_, part_d_, ticket_d_, counters_d_;
   int* counters_h_ = nullptr;   // pinned: [n_active, n_done]
 };
+
+// process-wide count of kernels launched by the library
+void count_launch(int n = 1);
 
 }  // namespace tem

@@ -65,6 +65,8 @@ struct GridView {
   const float* Sxf; const float* Syf; const float* Szf;
   const double* Me;         // [3][ncomp] lumped edge mass, 0 on boundary/padding entries
   const float* Mef;         // FP32 copy
+  const double* Wn;         // [ncomp] per node: sum over its edges of M_e / L_e^2 (0 on boundary nodes)
+  const float* Wnf;         // FP32 copy
 };
 
 }  // namespace tem
@@ -75,7 +77,7 @@ struct tem_grid {
   double origin[3];
   std::vector<double> sigma;        // host copy (for the adjoint)
   tem::DevBuf geo;                  // packed 1-D arrays
-  tem::DevBuf me;                   // Me (FP64) then Mef (FP32)
+  tem::DevBuf me;                   // Me (FP64), Mef (FP32), Wn (FP64), Wnf (FP32)
   tem::DevBuf sig;                  // sigma on the device (FP64)
   int device = 0;
 };
@@ -123,20 +125,24 @@ struct SlotDesc {
   GridView g;
   double xi_re, xi_im;      // shift
   void* x;                  // solution (T)
-  void* z;                  // preconditioned residual D^{-1} r (T)
+  void* r;                  // residual (T)
+  void* psi;                // nodal correction D_n^{-1} G^T r (T, one per node)
   void* p0; void* p1;       // search directions, double-buffered (T)
   void* q;                  // A p (T)
   int tiles_x, tiles_y, zchunks;  // stencil decomposition
   int nblk_stencil;         // tiles_x*tiles_y*zchunks
   int nblk_update;          // blocks of the update pass
+  int nblk_nodal;           // blocks of the nodal pass
   int blk_stencil0;         // first global block of this slot in the stencil launch
   int blk_update0;          // first global block of this slot in the update launch
+  int blk_nodal0;           // first global block of this slot in the nodal launch
   FastDiv div_nx, div_ny, div_nynz;
   // defect correction (FP64 outer loop)
   const double* f;          // right-hand side, real, edge layout (FP64)
   const double* rhs_c;      // complex right-hand side (adjoint), or NULL
   void* x64[2];             // FP64 iterate, double-buffered by the residual pass (MIXED) / x64[0] only (FP64)
   int x_fresh;              // 1: inner x is a correction starting at 0 (MIXED); 0: inner x is x64 (FP64)
+  int nodal;                // 1: preconditioner with the nodal-gradient correction; 0: Jacobi only
 };
 
 struct SlotScalars {
@@ -147,6 +153,7 @@ struct SlotScalars {
   double bb;                // ||b||^2 of this solve's right-hand side
   double tol2;              // stop when rr <= tol2 * bb
   int32_t active;           // 1 while iterating
+  int32_t pending;          // 1 after the residual pass armed an inner solve that the nodal pass has not started
   int32_t iters;
   int32_t max_iter;
   int32_t status;           // TEM_OK / TEM_ENOCONV / TEM_EBREAKDOWN

@@ -18,11 +18,12 @@ LIB_PATH = os.path.join(HERE, "libtem.so")
 
 TEM_OK, TEM_EINVAL, TEM_ENOMEM, TEM_ENOCONV, TEM_EBREAKDOWN, TEM_ETIMEOUT, TEM_ECUDA, TEM_EBUSY = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
+PRECOND_AUTO, PRECOND_JACOBI, PRECOND_NODAL = 0, 1, 2
 
 EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
             "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_adjoint",
-            "tem_state_destroy", "tem_apply_operator"]
+            "tem_state_destroy", "tem_apply_operator", "tem_launch_count", "tem_profile_passes"]
 
 
 class TEMError(RuntimeError):
@@ -34,7 +35,7 @@ class TEMError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32),
-                ("keep_state", C.c_int32), ("reserved", C.c_int32)]
+                ("keep_state", C.c_int32), ("precond", C.c_int32)]
 
 
 _lib = None
@@ -70,6 +71,10 @@ def lib():
     L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
     L.tem_state_destroy.argtypes = [C.c_void_p]
     L.tem_apply_operator.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+    L.tem_launch_count.argtypes = []
+    L.tem_launch_count.restype = C.c_int64
+    L.tem_profile_passes.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, C.c_int32,
+                                     C.c_int32, C.c_void_p, _dp, _dp]
     _lib = L
     return L
 
@@ -116,6 +121,8 @@ def default_options(**kw) -> Options:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": PREC_FP64, "mixed": PREC_MIXED}[v]
+        if k == "precond" and isinstance(v, str):
+            v = {"auto": PRECOND_AUTO, "jacobi": PRECOND_JACOBI, "nodal": PRECOND_NODAL}[v]
         setattr(o, k, v)
     return o
 
@@ -236,3 +243,22 @@ def apply_operator(grid: Grid, shifts, p, q, precision=PREC_FP64, stream=None):
     _check(lib().tem_apply_operator(grid.handle, _ptr(xi), len(shifts), C.c_void_p(p.data_ptr()),
                                     C.c_void_p(q.data_ptr()), int(precision), _stream(stream)),
            "tem_apply_operator")
+
+
+def launch_count() -> int:
+    """Kernels launched by libtem.so in this process so far."""
+    return int(lib().tem_launch_count())
+
+
+def profile_passes(grid: Grid, loop_xy, z_loop, shifts, precision=PREC_MIXED, n_iter=20, current=1.0, stream=None):
+    """Average CUDA-event time (ms) of the stencil, update and FP64 residual passes, and the
+    interior edges x shifts one launch processes (tem_profile_passes)."""
+    loop = _f64(loop_xy).reshape(-1, 2)
+    shifts = np.ascontiguousarray(shifts, dtype=np.complex128)
+    xi = shifts.view(np.float64)
+    ms = np.zeros(4)
+    units = np.zeros(1)
+    _check(lib().tem_profile_passes(grid.handle, _ptr(loop), len(loop), float(z_loop), float(current), _ptr(xi),
+                                    len(shifts), int(precision), int(n_iter), _stream(stream), _ptr(ms), _ptr(units)),
+           "tem_profile_passes")
+    return {"stencil_ms": ms[0], "update_ms": ms[1], "residual_ms": ms[2], "nodal_ms": ms[3], "units": units[0]}

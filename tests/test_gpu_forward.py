@@ -67,9 +67,11 @@ def test_tiny16_mixed_matches_oracle(tiny):
     _check(res.d, d_ref, S, 1e-5, 1e-9)
 
 
+@pytest.mark.parametrize("precond", ["jacobi", "nodal"])
 @pytest.mark.parametrize("dims", [(34, 10, 12), (20, 18, 40)])
-def test_ragged_grids_fp64(dims):
-    """Tiles of 32 x 8 nodes and 32-plane chunks with ragged tails in x, y and z."""
+def test_ragged_grids_fp64(dims, precond):
+    """Tiles of 32 x 8 nodes and 32-plane chunks with ragged tails in x, y and z; both
+    preconditioners (they change the iterates, not the solution)."""
     from paper_2506_11657_gb300 import tem
     nx, ny, nz = dims
     m = W.uniform_model(nx, 10.0, nz // 3, 0.02, 60.0, 1e-5, 1e-3, 9, 8, ny=ny, nz=nz)
@@ -77,7 +79,7 @@ def test_ragged_grids_fp64(dims):
     rx = np.array([[0.0, 0.0, 0.0], [12.0, 7.0, 0.0]])
     d_ref, S = _oracle(m, shifts, c, rx)
     grid = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma)
-    res = tem.forward(grid, m.loop_xy, m.z_loop, rx, shifts, c, tem.default_options(tol=1e-13))
+    res = tem.forward(grid, m.loop_xy, m.z_loop, rx, shifts, c, tem.default_options(tol=1e-13, precond=precond))
     _check(res.d, d_ref, S, 1e-6, 1e-10)
 
 

@@ -21,7 +21,7 @@ def _declared():
     for h in os.listdir(os.path.join(ROOT, "include")):
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
-            names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(tem_\w+)\s*\(", txt, re.M))
+            names |= set(re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+(tem_\w+)\s*\(", txt, re.M))
     return sorted(names)
 
 
