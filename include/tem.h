@@ -212,6 +212,25 @@ int tem_apply_operator(const tem_grid* grid, const double* xi, int64_t s,
                        const void* p_dev, void* q_dev, int32_t precision, void* cuda_stream);
 
 /*
+ * tem_apply_operator without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory, such as a
+ * host framework that owns all device memory through its own pool, or a latency-bound
+ * loop that must not risk the device-wide synchronisation cudaMalloc/cudaFree can cause.
+ * Same arguments, layout and result as tem_apply_operator (q[i] = (K - xi_i M) p[i]),
+ * with these differences:
+ *   - s <= 64 (TEM_EINVAL otherwise); the shifts are copied into one fixed 1 KB array
+ *     in device memory that the library defines statically, instead of a per-call buffer;
+ *   - the grid's device must be the current device (TEM_EINVAL otherwise);
+ *   - the first call on a device looks up that array's device address once
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call shares the array and leaves its shifts there; calls whose work
+ *     overlaps on the GPU (for example on two streams at once) race on it.
+ * Enqueued on cuda_stream; returns without synchronising.  Allocates nothing.
+ */
+int tem_apply_operator_noalloc(const tem_grid* grid, const double* xi, int64_t s,
+                               const void* p_dev, void* q_dev, int32_t precision, void* cuda_stream);
+
+/*
  * Number of CUDA kernels this library has launched in this process so far
  * (monotone; for launch accounting around a timed region).
  */

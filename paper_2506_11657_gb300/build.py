@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libtem.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["grid.cu", "solver.cu", "forward.cu", "serve.cu", "geometry.cpp", "poles.cpp"]
+SOURCES = ["grid.cu", "solver.cu", "forward.cu", "serve.cu", "noalloc.cu", "geometry.cpp", "poles.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,7 +23,8 @@ PRECOND_AUTO, PRECOND_JACOBI, PRECOND_NODAL = 0, 1, 2
 EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
             "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_adjoint",
-            "tem_state_destroy", "tem_apply_operator", "tem_launch_count", "tem_profile_passes"]
+            "tem_state_destroy", "tem_apply_operator", "tem_apply_operator_noalloc", "tem_launch_count",
+            "tem_profile_passes"]
 
 
 class TEMError(RuntimeError):
@@ -71,6 +72,8 @@ def lib():
     L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
     L.tem_state_destroy.argtypes = [C.c_void_p]
     L.tem_apply_operator.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
+    L.tem_apply_operator_noalloc.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
+                                             C.c_void_p]
     L.tem_launch_count.argtypes = []
     L.tem_launch_count.restype = C.c_int64
     L.tem_profile_passes.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, C.c_int32,
@@ -243,6 +246,16 @@ def apply_operator(grid: Grid, shifts, p, q, precision=PREC_FP64, stream=None):
     _check(lib().tem_apply_operator(grid.handle, _ptr(xi), len(shifts), C.c_void_p(p.data_ptr()),
                                     C.c_void_p(q.data_ptr()), int(precision), _stream(stream)),
            "tem_apply_operator")
+
+
+def apply_operator_noalloc(grid: Grid, shifts, p, q, precision=PREC_FP64, stream=None):
+    """tem_apply_operator_noalloc: same result as apply_operator, no device allocation
+    (at most 64 shifts; the shifts live in one array shared by all calls)."""
+    shifts = np.ascontiguousarray(shifts, dtype=np.complex128)
+    xi = shifts.view(np.float64)
+    _check(lib().tem_apply_operator_noalloc(grid.handle, _ptr(xi), len(shifts), C.c_void_p(p.data_ptr()),
+                                            C.c_void_p(q.data_ptr()), int(precision), _stream(stream)),
+           "tem_apply_operator_noalloc")
 
 
 def launch_count() -> int:
