@@ -37,12 +37,13 @@ WORKLOADS = {"randblock128": 128, "randblock64": 64}
 METRIC = "TEM forward models/s at 128^3 (mixed precision, FP64 residual 1e-12)"
 UNIT = "models/s"
 HBM_FALLBACK_GBS = 6800.0
-# algorithmic bytes per interior edge per shift of one launch, FP32 sweeps with the Jacobi
-# preconditioner (complex FP32 = 8 B):
+# algorithmic bytes per interior edge per shift of one launch, FP32 sweeps with the nodal
+# preconditioner (complex FP32 = 8 B; a nodal vector is 1/3 of an edge vector: 8/3 B per edge):
+NODE = 8.0 / 3.0
 PASS_BYTES = {
-    "stencil": 32.0,   # read r, p_old; write p, q
-    "update": 48.0,    # read x, r, p, q; write x, r
-    "nodal": 8.0,      # read r  ((r, z), ||r||; no nodal correction with Jacobi)
+    "stencil": 16.0 + 16.0 + 4.0 + 3 * NODE,   # read w, a_old, M_e, psi, b_old; write a, q, b
+    "update": 32.0 + 16.0 + 4.0 + 3 * NODE,    # read x, w, a, q, M_e, x_n, b; write x, w, x_n
+    "nodal": 8.0 + 4.0 + 4 * NODE,             # read x, M_e, x_n, cn, W_n (4 B/node); write psi
 }
 KERNEL_NAMES = {"stencil": "k_cocg_stencil<float>", "update": "k_cocg_update<float>",
                 "nodal": "k_cocg_nodal<float>"}
@@ -235,7 +236,7 @@ def main():
     shifts, c, uerr = tem.poles_residues(model.t, model.degree)
     stream = torch.cuda.current_stream(dev)
     grid = tem.Grid(model.hx, model.hy, model.hz, model.origin, model.sigma, stream=stream)
-    opt_mixed = tem.default_options(precision="mixed", tol=1e-12, inner_tol=0.1)
+    opt_mixed = tem.default_options(precision="mixed", tol=1e-12)
     opt_fp64 = tem.default_options(precision="fp64", tol=1e-12)
 
     def fwd(opt, keep=False):

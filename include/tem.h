@@ -73,7 +73,7 @@ typedef struct tem_options {
   int32_t precision;     /* TEM_PREC_FP64 (default) or TEM_PREC_MIXED */
   int32_t max_iter;      /* bound on COCG iterations per shift (default 20000) */
   double tol;            /* stop when ||f - A_i x_i||_2 <= tol ||f||_2, FP64 residual (default 1e-12) */
-  double inner_tol;      /* MIXED: relative residual reduction per FP32 inner solve (default 1e-1) */
+  double inner_tol;      /* MIXED: relative residual reduction per FP32 inner solve (default 1e-3) */
   int32_t max_outer;     /* MIXED: bound on FP64 defect-correction steps (default 40) */
   int32_t check_every;   /* iterations between host-side convergence polls (default 32) */
   int32_t keep_state;    /* nonzero: keep the solutions for tem_adjoint (state_out must be non-NULL) */
@@ -82,10 +82,12 @@ typedef struct tem_options {
 
 /* Preconditioner of the inner COCG sweeps. */
 enum {
-  TEM_PRECOND_AUTO = 0,    /* NODAL for FP64 sweeps, JACOBI for FP32 sweeps */
+  TEM_PRECOND_AUTO = 0,    /* NODAL */
   TEM_PRECOND_JACOBI = 1,  /* z = D^{-1} r,  D = diag(K) - xi M */
   TEM_PRECOND_NODAL = 2    /* z = D^{-1} r + G D_n^{-1} G^T r: Jacobi plus a correction in the
-                              nodal-gradient (near-null) space of K, D_n = -xi diag(G^T M G) */
+                              nodal-gradient (near-null) space of K, D_n = -xi diag(G^T M G).
+                              Relies on G^T b = 0 for the right-hand side b (true for closed
+                              loop sources and for receiver-adjoint sources) */
 };
 
 /* Default options (see the field comments). */
@@ -239,7 +241,7 @@ int64_t tem_launch_count(void);
 /*
  * Per-kernel timing of the solver's passes (measurement support; no paper
  * counterpart beyond the solves of Eq. (rmj)).  Sets up the batched solve of
- * tem_forward for `s` shifts (same loop source, precision as given), runs one
+ * tem_forward for `s` shifts (same loop source; precision and preconditioner as given), runs one
  * FP64 residual pass and then `n_iter` COCG iterations with CUDA events around
  * every launch on `cuda_stream`, and writes the average duration in ms of
  *   ms_out[0] : the stencil pass  (z = D^-1 r + G psi, p <- z + beta p, q <- A p, (p, q)),
@@ -250,7 +252,8 @@ int64_t tem_launch_count(void);
  * Slots that converge before n_iter stop being timed; use n_iter small enough.
  */
 int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop,
-                       double current, const double* xi, int64_t s, int32_t precision, int32_t n_iter,
+                       double current, const double* xi, int64_t s, int32_t precision, int32_t precond,
+                       int32_t n_iter,
                        void* cuda_stream, double* ms_out, double* units_out);
 
 #ifdef __cplusplus

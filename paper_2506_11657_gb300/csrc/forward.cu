@@ -48,7 +48,7 @@ int validate_poles(const double* xi, const double* c, int64_t s, int64_t K) {
 int use_nodal(const tem_options& o) {
   if (o.precond == TEM_PRECOND_NODAL) return 1;
   if (o.precond == TEM_PRECOND_JACOBI) return 0;
-  return o.precision == TEM_PREC_FP64 ? 1 : 0;
+  return 1;
 }
 
 int validate_options(const tem_options& o) {
@@ -305,7 +305,8 @@ int tem_apply_operator(const tem_grid* grid, const double* xi, int64_t s, const 
 int64_t tem_launch_count(void) { return tem::launch_count(); }
 
 int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop,
-                       double current, const double* xi, int64_t s, int32_t precision, int32_t n_iter,
+                       double current, const double* xi, int64_t s, int32_t precision, int32_t precond,
+                       int32_t n_iter,
                        void* cuda_stream, double* ms_out, double* units_out) {
   if (!grid || !xi || !ms_out || s < 1 || s > 64 || n_iter < 1 || n_iter > 100000) return TEM_EINVAL;
   if (precision != TEM_PREC_FP64 && precision != TEM_PREC_MIXED) return TEM_EINVAL;
@@ -330,6 +331,8 @@ int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_ve
   tem_options opt;
   tem_default_options(&opt);
   opt.precision = precision;
+  opt.precond = precond;
+  if (validate_options(opt) != TEM_OK) return TEM_EINVAL;
   opt.tol = 1e-300;   // nothing converges during the timed iterations
   opt.inner_tol = 1e-300;
   const size_t per = slot_vector_bytes(ncomp, precision);

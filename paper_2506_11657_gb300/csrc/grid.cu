@@ -205,7 +205,7 @@ void tem_default_options(tem_options* opt) {
   opt->precision = TEM_PREC_FP64;
   opt->max_iter = 20000;
   opt->tol = 1e-12;
-  opt->inner_tol = 1e-1;
+  opt->inner_tol = 1e-3;
   opt->max_outer = 40;
   opt->check_every = 32;
   opt->keep_state = 0;
@@ -230,23 +230,24 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   g->hz.assign(hz, hz + nz);
   for (int q = 0; q < 3; ++q) g->origin[q] = origin[q];
   cudaGetDevice(&g->device);
-  // packed 1-D geometry: L (3), S (3) in FP64, then in FP32
+  // packed 1-D geometry: L (3), S (3), 1/L (3) in FP64, then in FP32
   const int64_t n1 = nx + ny + nz;
-  std::vector<double> geo(6 * n1);
-  std::vector<float> geof(6 * n1);
+  std::vector<double> geo(9 * n1);
+  std::vector<float> geof(9 * n1);
   auto put = [&](int64_t off, const std::vector<double>& h) {
     const int64_t n = (int64_t)h.size();
     for (int64_t q = 0; q < n; ++q) {
       geo[off + q] = h[q];
       const double prev = q > 0 ? h[q - 1] : 0.0;
       geo[3 * n1 + off + q] = 0.5 * (prev + h[q]);  // dual length at node plane q
+      geo[6 * n1 + off + q] = 1.0 / h[q];
     }
   };
   put(0, g->hx);
   put(nx, g->hy);
   put(nx + ny, g->hz);
-  for (int64_t q = 0; q < 6 * n1; ++q) geof[q] = float(geo[q]);
-  int rc = g->geo.alloc(6 * n1 * (sizeof(double) + sizeof(float)), st);
+  for (int64_t q = 0; q < 9 * n1; ++q) geof[q] = float(geo[q]);
+  int rc = g->geo.alloc(9 * n1 * (sizeof(double) + sizeof(float)), st);
   if (rc == TEM_OK) rc = g->me.alloc(4 * ncell * (sizeof(double) + sizeof(float)), st);
   if (rc == TEM_OK) rc = g->sig.alloc(ncell * sizeof(double), st);
   if (rc != TEM_OK) {
@@ -254,7 +255,7 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
     return rc;
   }
   double* gd = g->geo.as<double>();
-  float* gf = reinterpret_cast<float*>(gd + 6 * n1);
+  float* gf = reinterpret_cast<float*>(gd + 9 * n1);
   if (cudaMemcpyAsync(gd, geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(gf, geof.data(), geof.size() * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) {
     set_last_error("geometry upload failed", __FILE__, __LINE__);
@@ -270,6 +271,8 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   v.Sx = gd + 3 * n1; v.Sy = gd + 3 * n1 + nx; v.Sz = gd + 3 * n1 + nx + ny;
   v.Lxf = gf; v.Lyf = gf + nx; v.Lzf = gf + nx + ny;
   v.Sxf = gf + 3 * n1; v.Syf = gf + 3 * n1 + nx; v.Szf = gf + 3 * n1 + nx + ny;
+  v.Rx = gd + 6 * n1; v.Ry = gd + 6 * n1 + nx; v.Rz = gd + 6 * n1 + nx + ny;
+  v.Rxf = gf + 6 * n1; v.Ryf = gf + 6 * n1 + nx; v.Rzf = gf + 6 * n1 + nx + ny;
   v.Me = g->me.as<double>();
   v.Wn = v.Me + 3 * ncell;
   v.Mef = reinterpret_cast<const float*>(v.Wn + ncell);

@@ -61,14 +61,15 @@ template <class T> __device__ __forceinline__ void st(void* base, int64_t idx, C
 // 1-D geometry accessors in the working precision
 template <class T> struct Geo;
 template <> struct Geo<double> {
-  const double *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Me;
-  __device__ Geo(const GridView& g) : Lx(g.Lx), Ly(g.Ly), Lz(g.Lz), Sx(g.Sx), Sy(g.Sy), Sz(g.Sz), Me(g.Me) {}
-  __device__ static const double* Wn(const GridView& g) { return g.Wn; }
+  const double *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Rx, *Ry, *Rz, *Me, *Wn;
+  __device__ Geo(const GridView& g)
+      : Lx(g.Lx), Ly(g.Ly), Lz(g.Lz), Sx(g.Sx), Sy(g.Sy), Sz(g.Sz), Rx(g.Rx), Ry(g.Ry), Rz(g.Rz), Me(g.Me), Wn(g.Wn) {}
 };
 template <> struct Geo<float> {
-  const float *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Me;
-  __device__ Geo(const GridView& g) : Lx(g.Lxf), Ly(g.Lyf), Lz(g.Lzf), Sx(g.Sxf), Sy(g.Syf), Sz(g.Szf), Me(g.Mef) {}
-  __device__ static const float* Wn(const GridView& g) { return g.Wnf; }
+  const float *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Rx, *Ry, *Rz, *Me, *Wn;
+  __device__ Geo(const GridView& g)
+      : Lx(g.Lxf), Ly(g.Lyf), Lz(g.Lzf), Sx(g.Sxf), Sy(g.Syf), Sz(g.Szf), Rx(g.Rxf), Ry(g.Ryf), Rz(g.Rzf),
+        Me(g.Mef), Wn(g.Wnf) {}
 };
 
 // Diagonal of K at edge (c, i, j, k) (valid, non-boundary edges only):
@@ -76,11 +77,9 @@ template <> struct Geo<float> {
 template <class T>
 __device__ __forceinline__ T diagK(const Geo<T>& G, int c, int i, int j, int k) {
   const T inv_mu0 = T(1.0 / TEM_MU0);
-  if (c == 0)
-    return G.Lx[i] * inv_mu0 * (G.Sz[k] * (T(1) / G.Ly[j] + T(1) / G.Ly[j - 1]) + G.Sy[j] * (T(1) / G.Lz[k] + T(1) / G.Lz[k - 1]));
-  if (c == 1)
-    return G.Ly[j] * inv_mu0 * (G.Sz[k] * (T(1) / G.Lx[i] + T(1) / G.Lx[i - 1]) + G.Sx[i] * (T(1) / G.Lz[k] + T(1) / G.Lz[k - 1]));
-  return G.Lz[k] * inv_mu0 * (G.Sx[i] * (T(1) / G.Ly[j] + T(1) / G.Ly[j - 1]) + G.Sy[j] * (T(1) / G.Lx[i] + T(1) / G.Lx[i - 1]));
+  if (c == 0) return G.Lx[i] * inv_mu0 * (G.Sz[k] * (G.Ry[j] + G.Ry[j - 1]) + G.Sy[j] * (G.Rz[k] + G.Rz[k - 1]));
+  if (c == 1) return G.Ly[j] * inv_mu0 * (G.Sz[k] * (G.Rx[i] + G.Rx[i - 1]) + G.Sx[i] * (G.Rz[k] + G.Rz[k - 1]));
+  return G.Lz[k] * inv_mu0 * (G.Sx[i] * (G.Ry[j] + G.Ry[j - 1]) + G.Sy[j] * (G.Rx[i] + G.Rx[i - 1]));
 }
 
 // Is edge (c, i, j, k) an unknown (not in the boundary, not padding)?
@@ -186,7 +185,7 @@ __device__ __forceinline__ void compute_faces(StencilSmem<T>& sm, int bk, int bk
     const int i = i0 - 1 + ii, j = j0 - 1 + jj;
     C2<T> fx = czero<T>(), fy = czero<T>(), fz = czero<T>();
     if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
-      const T rLx = T(1) / G.Lx[i], rLy = T(1) / G.Ly[j], rLz = T(1) / G.Lz[k];
+      const T rLx = G.Rx[i], rLy = G.Ry[j], rLz = G.Rz[k];
       // plane-k values around (ii, jj)
       const C2<T> px = sm.P[bk][0][jj][ii], py = sm.P[bk][1][jj][ii], pz = sm.P[bk][2][jj][ii];
       const C2<T> pz_j1 = sm.P[bk][2][jj + 1][ii];
@@ -214,7 +213,7 @@ __device__ __forceinline__ void own_faces_xy(const StencilSmem<T>& sm, int bk, i
   fy = czero<T>();
   if (k < 0 || k >= g.nz || i >= g.nx || j >= g.ny) return;
   const T inv_mu0 = T(1.0 / TEM_MU0);
-  const T rLx = T(1) / G.Lx[i], rLy = T(1) / G.Ly[j], rLz = T(1) / G.Lz[k];
+  const T rLx = G.Rx[i], rLy = G.Ry[j], rLz = G.Rz[k];
   const C2<T> px = sm.P[bk][0][jj][ii], py = sm.P[bk][1][jj][ii], pz = sm.P[bk][2][jj][ii];
   fx = (G.Sx[i] * inv_mu0) * (rLz * (py - sm.P[bk1][1][jj][ii]) + rLy * (sm.P[bk][2][jj + 1][ii] - pz));
   fy = (G.Sy[j] * inv_mu0) * (rLx * (pz - sm.P[bk][2][jj][ii + 1]) + rLz * (sm.P[bk1][0][jj][ii] - px));
@@ -245,6 +244,7 @@ __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView
     __syncthreads();
     if (i < g.nx && j < g.ny) {
       const int64_t base = i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+      pol.node(base, i, j, k);
       const C2<T> fx = sm.F[0][jj][ii], fy = sm.F[1][jj][ii], fz = sm.F[2][jj][ii];
       // x-edge
       if (edge_valid(0, i, j, k)) {
@@ -299,43 +299,48 @@ __device__ __forceinline__ void tile_of(const SlotDesc& d, int lb, int zchunk, i
 }
 
 // ---------------------------------------------------------- the preconditioner
-// Jacobi on the edges plus a nodal correction in the gradient (near-null) space of K
+// Jacobi on the edges plus a correction in the gradient (near-null) space of K
 // (the auxiliary-space idea of Hiptmair & Xu 2007):
 //     z = D^{-1} r + G psi,   psi = D_n^{-1} G^T r,
 //     D = diag(K) - xi M,     D_n = diag(G^T A G) = -xi diag(G^T M G) = -xi W,
-// with G the nodal gradient ((G phi)_e = (phi_end - phi_start) / L_e) on interior
-// nodes.  Both terms are complex symmetric, so COCG applies.
+// with G the gradient of interior-node potentials ((G phi)_e = (phi_end - phi_start) / L_e).
+// Both terms are complex symmetric, so COCG applies.  The iteration keeps every
+// direction split as p = a + G b (a on edges, b on nodes), so that
+//     A p = (K - xi M) a - xi M G b          (K G = 0 exactly, since curl grad = 0),
+// and K never acts on the large gradient part: in FP32 the rounding of a large
+// gradient would otherwise not be annihilated by K.
 template <class T>
 __device__ __forceinline__ C2<T> jacobi_D(const Geo<T>& G, int c, int i, int j, int k, int64_t idx, C2<T> xi) {
   return C2<T>(diagK<T>(G, c, i, j, k), T(0)) - (G.Me[idx] * xi);
 }
 
+// (G b)_e for edge (c, i, j, k) from nodal values; nodes at index n (boundary) hold 0.
 template <class T>
-__device__ __forceinline__ C2<T> precond_z(const Geo<T>& G, const GridView& g, int c, int i, int j, int k,
-                                           int64_t idx, C2<T> rv, C2<T> xi, const void* psi) {
-  C2<T> z = cdiv(rv, jacobi_D<T>(G, c, i, j, k, idx, xi));
-  if (!psi) return z;
-  const int64_t n0 = i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
-  const C2<T> ps = ld<T>(psi, n0);
-  C2<T> pe = czero<T>();
+__device__ __forceinline__ C2<T> grad_edge(const Geo<T>& G, const GridView& g, int c, int i, int j, int k,
+                                           int64_t n0, C2<T> b0, const void* bv, C2<T> beta, const void* bold,
+                                           const void* psi, bool use_beta) {
+  int64_t n1;
+  bool in;
   T rl;
-  if (c == 0) {
-    if (i + 1 < g.nx) pe = ld<T>(psi, n0 + 1);
-    rl = T(1) / G.Lx[i];
-  } else if (c == 1) {
-    if (j + 1 < g.ny) pe = ld<T>(psi, n0 + g.nx);
-    rl = T(1) / G.Ly[j];
-  } else {
-    if (k + 1 < g.nz) pe = ld<T>(psi, n0 + (int64_t)g.nx * g.ny);
-    rl = T(1) / G.Lz[k];
+  if (c == 0) { in = i + 1 < g.nx; n1 = n0 + 1; rl = G.Rx[i]; }
+  else if (c == 1) { in = j + 1 < g.ny; n1 = n0 + g.nx; rl = G.Ry[j]; }
+  else { in = k + 1 < g.nz; n1 = n0 + (int64_t)g.nx * g.ny; rl = G.Rz[k]; }
+  C2<T> b1 = czero<T>();
+  if (in) {
+    if (bv) b1 = ld<T>(bv, n1);
+    else {
+      b1 = ld<T>(psi, n1);
+      if (use_beta) b1 = b1 + cmul(beta, ld<T>(bold, n1));
+    }
   }
-  return z + rl * (pe - ps);
+  return rl * (b1 - b0);
 }
 
-// ------------------------------------- pass A: p <- z + beta p; q <- A p; (p, q) -> alpha
+// ---------------------- pass A: a <- w + beta a, b <- psi + beta b, q <- A (a + G b), (p, q)
 template <class T>
 struct CocgStencilPol {
-  const void* r; const void* psi; const void* pold; void* pnew; void* q;
+  const void* w; const void* aold; void* anew; void* q;
+  const void* psi; const void* bold; void* bnew;   // nodal part (NULL with Jacobi only)
   C2<T> beta; bool use_beta;
   C2<T> xi;
   Geo<T> G;
@@ -343,14 +348,33 @@ struct CocgStencilPol {
   C2<T> acc;
   __device__ CocgStencilPol(const GridView& gv) : G(gv), g(&gv) {}
   __device__ C2<T> load(int c, int i, int j, int k, int64_t idx, bool own) {
-    if (!edge_valid(c, i, j, k)) return czero<T>();  // boundary: p stays 0 (buffers start zeroed)
-    C2<T> v = precond_z<T>(G, *g, c, i, j, k, idx, ld<T>(r, idx), xi, psi);
-    if (use_beta) v = v + cmul(beta, ld<T>(pold, idx));
-    if (own) st<T>(pnew, idx, v);
+    if (!edge_valid(c, i, j, k)) return czero<T>();  // boundary: a stays 0 (buffers start zeroed)
+    C2<T> v = ld<T>(w, idx);
+    if (use_beta) v = v + cmul(beta, ld<T>(aold, idx));
+    if (own) st<T>(anew, idx, v);
     return v;
   }
-  __device__ void edge(int, int64_t idx, int, int, int, C2<T> p, C2<T> kp) {
-    const C2<T> qv = kp - cmul(xi, G.Me[idx] * p);
+  // (G b) on the three edges leaving the thread's own node of the current plane
+  C2<T> gb[3];
+  __device__ C2<T> bval(int64_t n) const {
+    C2<T> v = ld<T>(psi, n);
+    if (use_beta) v = v + cmul(beta, ld<T>(bold, n));
+    return v;
+  }
+  __device__ void node(int64_t n, int i, int j, int k) {   // once per own node, before its edges
+    if (!psi) return;
+    const C2<T> b0 = bval(n);
+    st<T>(bnew, n, b0);
+    const C2<T> bx = i + 1 < g->nx ? bval(n + 1) : czero<T>();
+    const C2<T> by = j + 1 < g->ny ? bval(n + g->nx) : czero<T>();
+    const C2<T> bz = k + 1 < g->nz ? bval(n + (int64_t)g->nx * g->ny) : czero<T>();
+    gb[0] = G.Rx[i] * (bx - b0);
+    gb[1] = G.Ry[j] * (by - b0);
+    gb[2] = G.Rz[k] * (bz - b0);
+  }
+  __device__ void edge(int c, int64_t idx, int, int, int, C2<T> a, C2<T> ka) {
+    const C2<T> p = psi ? a + gb[c] : a;
+    const C2<T> qv = ka - cmul(xi, G.Me[idx] * p);
     st<T>(q, idx, qv);
     acc = acc + cmul(p, qv);
   }
@@ -368,10 +392,12 @@ __global__ void __launch_bounds__(NT) k_cocg_stencil(BatchArgs A) {
   int i0, j0, k0, k1;
   tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
   CocgStencilPol<T> pol(d.g);
-  pol.r = d.r;
+  pol.w = d.w;
+  pol.aold = S->parity ? d.a1 : d.a0;
+  pol.anew = S->parity ? d.a0 : d.a1;
   pol.psi = d.nodal ? d.psi : nullptr;
-  pol.pold = S->parity ? d.p1 : d.p0;
-  pol.pnew = S->parity ? d.p0 : d.p1;
+  pol.bold = S->parity ? d.b1 : d.b0;
+  pol.bnew = S->parity ? d.b0 : d.b1;
   pol.q = d.q;
   pol.beta = C2<T>(T(S->beta_re), T(S->beta_im));
   pol.use_beta = !(S->beta_re == 0.0 && S->beta_im == 0.0);
@@ -399,36 +425,146 @@ __global__ void __launch_bounds__(NT) k_cocg_stencil(BatchArgs A) {
   }
 }
 
-// ------------------------------------------------- pass B: x += alpha p; r -= alpha q
-// A pure stream over the slot's entries: boundary entries hold p = q = 0 and stay put.
-template <class T>
-__global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
-  const int slot = A.ublk2slot[blockIdx.x];
-  const SlotScalars* S = A.sc + slot;
-  if (!S->active) return;
-  const SlotDesc& d = A.slots[slot];
-  const int lb = blockIdx.x - d.blk_update0;
-  const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
-  const bool first = d.x_fresh && S->iters == 0;  // MIXED: the correction starts at 0
-  const void* p = S->parity ? d.p0 : d.p1;         // the direction written by pass A
-  void* x = d.x;
-  void* r = d.r;
-  const void* q = d.q;
-  const int64_t n = 3 * d.g.ncomp;
-  const int64_t per = (n + d.nblk_update - 1) / d.nblk_update;
-  const int64_t e0 = (int64_t)lb * per, e1 = min(n, e0 + per);
-  for (int64_t e = e0 + threadIdx.x; e < e1; e += NT) {
-    const C2<T> pv = ld<T>(p, e);
-    C2<T> xv = cmul(alpha, pv);
-    if (!first) xv = xv + ld<T>(x, e);
-    st<T>(x, e, xv);
-    st<T>(r, e, ld<T>(r, e) - cmul(alpha, ld<T>(q, e)));
+// Convergence test and the next beta, from rho = (r, z) and rr = ||r||^2 (last CTA only).
+__device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, double rho_re, double rho_im,
+                                                 double rr) {
+  S->iters += 1;
+  S->rr = rr;
+  bool done = false;
+  if (!isfinite(rho_re) || !isfinite(rho_im) || !isfinite(rr)) {
+    S->status = TEM_EBREAKDOWN;
+    done = true;
+  } else if (rr <= S->tol2) {
+    done = true;  // converged
+  } else if (S->iters >= S->max_iter) {
+    S->status = TEM_ENOCONV;
+    done = true;
+  } else {
+    const double den = S->rho_re * S->rho_re + S->rho_im * S->rho_im;
+    if (!(den > 0.0)) {
+      S->status = TEM_EBREAKDOWN;
+      done = true;
+    } else {
+      S->beta_re = (rho_re * S->rho_re + rho_im * S->rho_im) / den;
+      S->beta_im = (rho_im * S->rho_re - rho_re * S->rho_im) / den;
+      S->rho_re = rho_re;
+      S->rho_im = rho_im;
+      S->parity ^= 1;
+    }
+  }
+  if (done) {
+    S->active = 0;
+    S->total_iters += S->iters;
+    atomicSub(n_active, 1);
   }
 }
 
-// --------------------- pass C: psi = D_n^{-1} G^T r;  rho = (r, z);  ||r||^2 -> beta, stop
-// Each node owns the three edges that leave it, so the edge part of (r, z) = r^T D^{-1} r
-// and ||r||^2 are summed once; (r, G psi) = (G^T r, psi) is the nodal part.
+// ---------- pass B: x += alpha a, x_n += alpha b, r = D w - alpha q, w = r / D; (r, D^-1 r), ||r||
+// Entries [0, 3n) are edges, [3n, 4n) nodes of the slot.
+template <class T>
+__global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
+  __shared__ double red[NT / 32 * 4];
+  const int slot = A.ublk2slot[blockIdx.x];
+  SlotScalars* S = A.sc + slot;
+  if (!S->active) return;
+  const SlotDesc& d = A.slots[slot];
+  const GridView& g = d.g;
+  const Geo<T> G(g);
+  const int lb = blockIdx.x - d.blk_update0;
+  const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
+  const C2<T> xi(T(d.xi_re), T(d.xi_im));
+  const bool first = S->iters == 0;                 // the correction starts at 0
+  const void* a = S->parity ? d.a0 : d.a1;          // the direction written by pass A
+  const void* b = S->parity ? d.b0 : d.b1;
+  const uint32_t ne = (uint32_t)(3 * g.ncomp);
+  const uint32_t n = ne + (d.nodal ? (uint32_t)g.ncomp : 0u);
+  const uint32_t per = (n + d.nblk_update - 1) / d.nblk_update;
+  const uint32_t e0 = (uint32_t)lb * per, e1 = min(n, e0 + per);
+  C2<T> rz = czero<T>();
+  T rr = T(0);
+  for (uint32_t e = e0 + threadIdx.x; e < e1; e += NT) {
+    if (e >= ne) {  // nodal part of the correction
+      const uint32_t m = e - ne;
+      C2<T> xv = cmul(alpha, ld<T>(b, m));
+      if (!first) xv = xv + ld<T>(d.xn, m);
+      st<T>(d.xn, m, xv);
+      continue;
+    }
+    const uint32_t row = fdiv(e, d.div_nx);
+    const int i = int(e - row * (uint32_t)g.nx);
+    const uint32_t c = fdiv(row, d.div_nynz);
+    const uint32_t jk = row - c * (uint32_t)(g.ny * g.nz);
+    const uint32_t k = fdiv(jk, d.div_ny);
+    const int j = int(jk - k * (uint32_t)g.ny);
+    if (!edge_valid(int(c), i, j, int(k))) continue;
+    C2<T> xv = cmul(alpha, ld<T>(a, e));
+    if (!first) xv = xv + ld<T>(d.x, e);
+    st<T>(d.x, e, xv);
+    const C2<T> D = jacobi_D<T>(G, int(c), i, j, int(k), e, xi);
+    const C2<T> r = cmul(D, ld<T>(d.w, e)) - cmul(alpha, ld<T>(d.q, e));
+    const C2<T> wv = cdiv(r, D);
+    st<T>(d.w, e, wv);
+    rz = rz + cmul(r, wv);
+    rr += r.re * r.re + r.im * r.im;
+  }
+  double v[3] = {double(rz.re), double(rz.im), double(rr)};
+  block_sum<3, NT>(v, red);
+  double* part = A.part + (int64_t)slot * A.part_stride;
+  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_update, lb)) {
+    double tot[3];
+    sum_partials<3, NT>(part, d.nblk_update, tot, red);
+    if (threadIdx.x != 0) return;
+    if (d.nodal) {  // the nodal pass adds (G^T r, psi) and decides
+      S->rhoe_re = tot[0];
+      S->rhoe_im = tot[1];
+      S->rr = tot[2];
+    } else {
+      finish_iteration(S, A.n_active, tot[0], tot[1], tot[2]);
+    }
+  }
+}
+
+// ------------------------------ pass C: psi = D_n^{-1} G^T r;  rho = (r, D^-1 r) + (G^T r, psi)
+// G^T r is not formed from r: in the air D_n is tiny, and rounding in the divergence of r
+// would be amplified by 1/D_n.  Instead, with G^T K = 0 (curl grad = 0) and G^T b_outer = 0
+// (the loop source and the adjoint sources are divergence-free), the residual of the inner
+// solve A d = s r64 obeys exactly
+//     G^T r_k = s xi G^T M x64 + xi G^T M d_k,    d_k = d_e + G d_n,
+// so the first term (cn) is formed once, in FP64, when the solve starts.
+template <class T>
+__device__ __forceinline__ C2<T> nodal_at(const void* v, const GridView& g, int i, int j, int k, int64_t n) {
+  // interior nodes only hold values; the boundary is zero
+  if (i <= 0 || j <= 0 || k <= 0 || i >= g.nx || j >= g.ny || k >= g.nz) return czero<T>();
+  return ld<T>(v, n);
+}
+
+// (G^T M v)_n at interior node n for an edge field v = v_e + G v_n (v_n may be NULL).
+template <class T, class TV>
+__device__ __forceinline__ C2<T> div_Mv(const Geo<T>& G, const GridView& g, const void* ve, const void* vn,
+                                        int i, int j, int k, int64_t n) {
+  const int64_t nc = g.ncomp, sy = g.nx, sz = (int64_t)g.nx * g.ny;
+  auto edge_val = [&](int64_t e) {
+    const C2<TV> v = ld<TV>(ve, e);
+    return C2<T>(T(v.re), T(v.im));
+  };
+  auto node_val = [&](int ii, int jj, int kk, int64_t m) {
+    if (!vn) return czero<T>();
+    const C2<TV> v = nodal_at<TV>(vn, g, ii, jj, kk, m);
+    return C2<T>(T(v.re), T(v.im));
+  };
+  const C2<T> v0 = node_val(i, j, k, n);
+  // the six edges at n: x (i-1 -> i), x (i -> i+1), and likewise in y and z
+  const C2<T> xm = edge_val(n - 1) + G.Rx[i - 1] * (v0 - node_val(i - 1, j, k, n - 1));
+  const C2<T> xp = edge_val(n) + G.Rx[i] * (node_val(i + 1, j, k, n + 1) - v0);
+  const C2<T> ym = edge_val(nc + n - sy) + G.Ry[j - 1] * (v0 - node_val(i, j - 1, k, n - sy));
+  const C2<T> yp = edge_val(nc + n) + G.Ry[j] * (node_val(i, j + 1, k, n + sy) - v0);
+  const C2<T> zm = edge_val(2 * nc + n - sz) + G.Rz[k - 1] * (v0 - node_val(i, j, k - 1, n - sz));
+  const C2<T> zp = edge_val(2 * nc + n) + G.Rz[k] * (node_val(i, j, k + 1, n + sz) - v0);
+  return (G.Rx[i - 1] * G.Me[n - 1]) * xm - (G.Rx[i] * G.Me[n]) * xp +
+         (G.Ry[j - 1] * G.Me[nc + n - sy]) * ym - (G.Ry[j] * G.Me[nc + n]) * yp +
+         (G.Rz[k - 1] * G.Me[2 * nc + n - sz]) * zm - (G.Rz[k] * G.Me[2 * nc + n]) * zp;
+}
+
 template <class T>
 __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A, int init_only) {
   __shared__ double red[NT / 32 * 4];
@@ -437,117 +573,104 @@ __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A, int init_only) {
   const bool pend = S->pending != 0;
   if (!(pend || (S->active && !init_only))) return;
   const SlotDesc& d = A.slots[slot];
+  if (!d.nodal) return;
   const GridView& g = d.g;
   const Geo<T> G(g);
+  const Geo<double> G64(g);
   const int lb = blockIdx.x - d.blk_nodal0;
   const C2<T> xi(T(d.xi_re), T(d.xi_im));
-  const T* Wn = Geo<T>::Wn(g);
+  const C2<double> xi64(d.xi_re, d.xi_im);
+  const double sc = 1.0 / S->inv_scale_prev;   // scale of this solve's right-hand side
+  const void* x64 = d.x64[S->xcur];
   const uint32_t nn = (uint32_t)g.ncomp;
   const uint32_t per = (nn + d.nblk_nodal - 1) / d.nblk_nodal;
   const uint32_t n0 = (uint32_t)lb * per, n1 = min(nn, n0 + per);
-  const int64_t nc = g.ncomp;
-  const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
   C2<T> rho = czero<T>();
-  T rr = T(0);
   for (uint32_t n = n0 + threadIdx.x; n < n1; n += NT) {
     const uint32_t row = fdiv(n, d.div_nx);
     const int i = int(n - row * (uint32_t)g.nx);
     const uint32_t k = fdiv(row, d.div_ny);
     const int j = int(row - k * (uint32_t)g.ny);
-    // own edges
-    const C2<T> rx = ld<T>(d.r, n), ry = ld<T>(d.r, nc + n), rz = ld<T>(d.r, 2 * nc + n);
-    if (edge_valid(0, i, j, int(k))) rho = rho + cmul(rx, cdiv(rx, jacobi_D<T>(G, 0, i, j, int(k), n, xi)));
-    if (edge_valid(1, i, j, int(k))) rho = rho + cmul(ry, cdiv(ry, jacobi_D<T>(G, 1, i, j, int(k), nc + n, xi)));
-    if (edge_valid(2, i, j, int(k))) rho = rho + cmul(rz, cdiv(rz, jacobi_D<T>(G, 2, i, j, int(k), 2 * nc + n, xi)));
-    rr += rx.re * rx.re + rx.im * rx.im + ry.re * ry.re + ry.im * ry.im + rz.re * rz.re + rz.im * rz.im;
     C2<T> ps = czero<T>();
-    if (d.nodal && i > 0 && j > 0 && k > 0) {
-      // (G^T r)_n = sum over the 6 edges at n of (+1 if n ends the edge, -1 if it starts it) r_e / L_e
-      const C2<T> div = (T(1) / G.Lx[i - 1]) * ld<T>(d.r, n - 1) - (T(1) / G.Lx[i]) * rx +
-                        (T(1) / G.Ly[j - 1]) * ld<T>(d.r, nc + n - sy) - (T(1) / G.Ly[j]) * ry +
-                        (T(1) / G.Lz[k - 1]) * ld<T>(d.r, 2 * nc + n - sz) - (T(1) / G.Lz[k]) * rz;
-      const C2<T> Dn = Wn[n] * C2<T>(-xi.re, -xi.im);
-      ps = cdiv(div, Dn);
-      rho = rho + cmul(div, ps);
+    if (i > 0 && j > 0 && k > 0) {
+      C2<T> dv;
+      if (pend) {  // start of a solve: cn = s xi G^T M x64 in FP64; d = 0
+        const C2<double> c0 = (sc * 1.0) * cmul(xi64, div_Mv<double, double>(G64, g, x64, nullptr, i, j, int(k), n));
+        dv = C2<T>(T(c0.re), T(c0.im));
+        st<T>(d.cn, n, dv);
+      } else {
+        dv = ld<T>(d.cn, n) + cmul(xi, div_Mv<T, T>(G, g, d.x, d.xn, i, j, int(k), n));
+      }
+      const C2<T> Dn = G.Wn[n] * C2<T>(-xi.re, -xi.im);
+      ps = cdiv(dv, Dn);
+      rho = rho + cmul(dv, ps);
     }
-    if (d.nodal) st<T>(d.psi, n, ps);
+    st<T>(d.psi, n, ps);
   }
-  double v[3] = {double(rho.re), double(rho.im), double(rr)};
-  block_sum<3, NT>(v, red);
+  double v[2] = {double(rho.re), double(rho.im)};
+  block_sum<2, NT>(v, red);
   double* part = A.part + (int64_t)slot * A.part_stride;
-  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_nodal, lb)) {
-    double tot[3];
-    sum_partials<3, NT>(part, d.nblk_nodal, tot, red);
+  if (publish_partial<2>(v, part, A.ticket + slot, d.nblk_nodal, lb)) {
+    double tot[2];
+    sum_partials<2, NT>(part, d.nblk_nodal, tot, red);
     if (threadIdx.x != 0) return;
-    S->rr = tot[2];
+    const double rre = S->rhoe_re + tot[0], rim = S->rhoe_im + tot[1];
     if (pend) {  // first nodal pass of an inner solve: rho_0, beta = 0
       S->pending = 0;
-      S->rho_re = tot[0];
-      S->rho_im = tot[1];
+      S->rho_re = rre;
+      S->rho_im = rim;
       S->beta_re = 0.0;
       S->beta_im = 0.0;
       S->active = 1;
       return;
     }
-    S->iters += 1;
-    bool done = false;
-    if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
-      S->status = TEM_EBREAKDOWN;
-      done = true;
-    } else if (tot[2] <= S->tol2) {
-      done = true;  // converged
-    } else if (S->iters >= S->max_iter) {
-      S->status = TEM_ENOCONV;
-      done = true;
-    } else {
-      const double den = S->rho_re * S->rho_re + S->rho_im * S->rho_im;
-      if (!(den > 0.0)) {
-        S->status = TEM_EBREAKDOWN;
-        done = true;
-      } else {
-        S->beta_re = (tot[0] * S->rho_re + tot[1] * S->rho_im) / den;
-        S->beta_im = (tot[1] * S->rho_re - tot[0] * S->rho_im) / den;
-        S->rho_re = tot[0];
-        S->rho_im = tot[1];
-        S->parity ^= 1;
-      }
-    }
-    if (done) {
-      S->active = 0;
-      S->total_iters += S->iters;
-      atomicSub(A.n_active, 1);
-    }
+    finish_iteration(S, A.n_active, rre, rim, S->rr);
   }
 }
 
 // ------------------------------- FP64 residual pass (the outer defect-correction step)
-// x <- x64[cur] (+ inv_scale_prev * delta for MIXED, written to x64[cur^1]);
-// r = b - A x in FP64;  r_inner = scale * r in the inner precision TI;
+// x <- x64[cur] + inv_scale_prev (d_e + G d_n)  (the last inner correction), into x64[cur^1];
+// r = b - A x in FP64;  w_inner = (scale r) / D  in the inner precision TI;
 // then (last CTA) either finish the slot or arm the next inner COCG solve.
 template <class TI>
 struct ResidualPol {
-  const void* xcur; const void* delta; void* xnext; double inv_sc; bool upd;
+  const void* xcur; const void* de; const void* dn; void* xnext; double inv_sc; bool upd;
   const double* f; const void* rhs_c;
   C2<double> xi; const double* Me;
-  void* rin; double scale;
-  double rr;
-  __device__ C2<double> load(int, int, int, int, int64_t idx, bool own) {
+  Geo<TI> GI; Geo<double> G; const GridView* g; TI xr, xim;
+  void* win; double scale;
+  double rr, rz_re, rz_im;
+  __device__ ResidualPol(const GridView& gv) : GI(gv), G(gv), g(&gv) {}
+  __device__ C2<double> load(int c, int i, int j, int k, int64_t idx, bool own) {
     C2<double> x = ld<double>(xcur, idx);
-    if (upd) {
-      const C2<TI> dv = ld<TI>(delta, idx);
-      x = x + inv_sc * C2<double>(double(dv.re), double(dv.im));
+    if (upd && edge_valid(c, i, j, k)) {
+      const C2<TI> dv = ld<TI>(de, idx);
+      C2<double> corr(double(dv.re), double(dv.im));
+      if (dn) {
+        const int64_t n0 = i + (int64_t)g->nx * (j + (int64_t)g->ny * k);
+        const C2<TI> b0 = ld<TI>(dn, n0);
+        const C2<TI> gb = grad_edge<TI>(GI, *g, c, i, j, k, n0, b0, dn, czero<TI>(), nullptr, nullptr, false);
+        corr = corr + C2<double>(double(gb.re), double(gb.im));
+      }
+      x = x + inv_sc * corr;
       if (own) st<double>(xnext, idx, x);
     }
     return x;
   }
-  __device__ void edge(int, int64_t idx, int, int, int, C2<double> xv, C2<double> kx) {
+  __device__ void node(int64_t, int, int, int) {}
+  __device__ void edge(int c, int64_t idx, int i, int j, int k, C2<double> xv, C2<double> kx) {
     const C2<double> ax = kx - cmul(xi, Me[idx] * xv);
     const C2<double> b = rhs_c ? ld<double>(rhs_c, idx) : C2<double>(f[idx], 0.0);
     const C2<double> r = b - ax;
     rr += r.re * r.re + r.im * r.im;
-    st<TI>(rin, idx, C2<TI>(TI(scale * r.re), TI(scale * r.im)));
+    const C2<TI> rs(TI(scale * r.re), TI(scale * r.im));
+    const C2<TI> wv = cdiv(rs, jacobi_D<TI>(GI, c, i, j, k, idx, C2<TI>(xr, xim)));
+    st<TI>(win, idx, wv);
+    const C2<TI> pz = cmul(rs, wv);
+    rz_re += double(pz.re);
+    rz_im += double(pz.im);
   }
-  __device__ void edge_invalid(int64_t idx) { st<TI>(rin, idx, czero<TI>()); }
+  __device__ void edge_invalid(int64_t idx) { st<TI>(win, idx, czero<TI>()); }
 };
 
 template <class TI>
@@ -560,26 +683,29 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
   const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
   tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
-  ResidualPol<TI> pol;
-  pol.upd = d.x_fresh && S->outer > 0;
+  ResidualPol<TI> pol(d.g);
+  pol.upd = S->outer > 0;
   pol.xcur = d.x64[S->xcur];
   pol.xnext = d.x64[S->xcur ^ 1];
-  pol.delta = d.x;
+  pol.de = d.x;
+  pol.dn = d.nodal ? d.xn : nullptr;
   pol.inv_sc = S->inv_scale_prev;
   pol.f = d.f;
   pol.rhs_c = d.rhs_c;
   pol.xi = C2<double>(d.xi_re, d.xi_im);
   pol.Me = d.g.Me;
-  pol.rin = d.r;
+  pol.xr = TI(d.xi_re);
+  pol.xim = TI(d.xi_im);
+  pol.win = d.w;
   pol.scale = S->scale;
-  pol.rr = 0.0;
+  pol.rr = pol.rz_re = pol.rz_im = 0.0;
   stencil_march<double>(sm, d.g, pol, i0, j0, k0, k1);
-  double v[1] = {pol.rr};
-  block_sum<1, NT>(v, sm.red);
+  double v[3] = {pol.rr, pol.rz_re, pol.rz_im};
+  block_sum<3, NT>(v, sm.red);
   double* part = A.part + (int64_t)slot * A.part_stride;
-  if (publish_partial<1>(v, part, A.ticket + slot, d.nblk_stencil, lb)) {
-    double tot[1];
-    sum_partials<1, NT>(part, d.nblk_stencil, tot, sm.red);
+  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_stencil, lb)) {
+    double tot[3];
+    sum_partials<3, NT>(part, d.nblk_stencil, tot, sm.red);
     if (threadIdx.x != 0) return;
     if (pol.upd) S->xcur ^= 1;
     S->rr64 = tot[0];
@@ -601,18 +727,27 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
       atomicAdd(n_done, 1);
       return;
     }
-    // arm the inner solve on  A delta = scale * r  (MIXED)  or continue x (FP64);
-    // the nodal pass computes rho_0 and starts it
+    // arm the inner solve on  A d = scale * r  (d = d_e + G d_n starts at 0)
     const double sc = S->scale;
     S->bb = sc * sc * tot[0];
     const double want = 0.25 * S->tol_outer2 / tot[0];   // reach 1/2 of the final target
-    const double rel2 = d.x_fresh ? fmax(S->inner_rel2, want) : want;
+    const double rel2 = d.fp64_inner ? want : fmax(S->inner_rel2, want);
     S->tol2 = rel2 * S->bb;
     S->iters = 0;
     S->parity = 0;
     S->inv_scale_prev = 1.0 / sc;
-    if (d.x_fresh) S->scale = 1.0 / sqrt(tot[0]);
-    S->pending = 1;
+    S->scale = 1.0 / sqrt(tot[0]);
+    S->rhoe_re = tot[1];
+    S->rhoe_im = tot[2];
+    S->beta_re = 0.0;
+    S->beta_im = 0.0;
+    if (d.nodal) {
+      S->pending = 1;            // the nodal pass adds (G^T r, psi) to rho_0 and starts the solve
+    } else {
+      S->rho_re = tot[1];
+      S->rho_im = tot[2];
+      S->active = 1;
+    }
     atomicAdd(A.n_active, 1);
   }
 }
@@ -622,6 +757,7 @@ template <class T>
 struct ApplyPol {
   const void* p; void* q; C2<T> xi; const T* Me;
   __device__ C2<T> load(int, int, int, int, int64_t idx, bool) { return ld<T>(p, idx); }
+  __device__ void node(int64_t, int, int, int) {}
   __device__ void edge(int, int64_t idx, int, int, int, C2<T> pv, C2<T> kp) {
     st<T>(q, idx, kp - cmul(xi, Me[idx] * pv));
   }

@@ -23,31 +23,27 @@ int64_t launch_count() { return g_launches.load(); }
 
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Per slot: x64[2] (FP64 edge vectors), then x, w, a0, a1, q (inner edge vectors) and
+// xn, psi, b0, b1, cn (inner nodal vectors) in the inner precision.
 size_t slot_vector_bytes(int64_t ncomp, int precision) {
-  const size_t n = 3 * (size_t)ncomp;
-  const size_t v64 = align256(n * 16), n64 = align256((size_t)ncomp * 16);
-  if (precision == TEM_PREC_FP64) return 5 * v64 + n64;  // x64, r, p0, p1, q; psi
-  const size_t v32 = align256(n * 8), n32 = align256((size_t)ncomp * 8);
-  return 2 * v64 + 5 * v32 + n32;                        // x64[2], d, r, p0, p1, q; psi
+  const size_t es = precision == TEM_PREC_FP64 ? 16 : 8;
+  const size_t v64 = align256(3 * (size_t)ncomp * 16);
+  const size_t ve = align256(3 * (size_t)ncomp * es), vn = align256((size_t)ncomp * es);
+  return 2 * v64 + 5 * ve + 5 * vn;
 }
 
 SlotVectors carve_slot(void* base, int64_t ncomp, int precision) {
-  const size_t n = 3 * (size_t)ncomp;
+  const size_t es = precision == TEM_PREC_FP64 ? 16 : 8;
+  const size_t v64 = align256(3 * (size_t)ncomp * 16);
+  const size_t ve = align256(3 * (size_t)ncomp * es), vn = align256((size_t)ncomp * es);
   char* b = static_cast<char*>(base);
   SlotVectors v;
-  const size_t v64 = align256(n * 16);
-  if (precision == TEM_PREC_FP64) {
-    v.x64[0] = b; v.x64[1] = b;
-    v.inner_x = b;
-    v.r = b + v64; v.p0 = b + 2 * v64; v.p1 = b + 3 * v64; v.q = b + 4 * v64;
-    v.psi = b + 5 * v64;
-  } else {
-    const size_t v32 = align256(n * 8);
-    v.x64[0] = b; v.x64[1] = b + v64;
-    char* c = b + 2 * v64;
-    v.inner_x = c; v.r = c + v32; v.p0 = c + 2 * v32; v.p1 = c + 3 * v32; v.q = c + 4 * v32;
-    v.psi = c + 5 * v32;
-  }
+  v.x64[0] = b;
+  v.x64[1] = b + v64;
+  char* e = b + 2 * v64;
+  v.x = e; v.w = e + ve; v.a0 = e + 2 * ve; v.a1 = e + 3 * ve; v.q = e + 4 * ve;
+  char* n = e + 5 * ve;
+  v.xn = n; v.psi = n + vn; v.b0 = n + 2 * vn; v.b1 = n + 3 * vn; v.cn = n + 4 * vn;
   return v;
 }
 
@@ -63,17 +59,21 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
   d.g = g;
   d.xi_re = xi_re;
   d.xi_im = xi_im;
-  d.x = v.inner_x;
-  d.r = v.r;
-  d.psi = v.psi;
-  d.p0 = v.p0;
-  d.p1 = v.p1;
+  d.x = v.x;
+  d.w = v.w;
+  d.a0 = v.a0;
+  d.a1 = v.a1;
   d.q = v.q;
+  d.xn = v.xn;
+  d.psi = v.psi;
+  d.b0 = v.b0;
+  d.b1 = v.b1;
+  d.cn = v.cn;
   d.x64[0] = v.x64[0];
   d.x64[1] = v.x64[1];
   d.f = f_real;
   d.rhs_c = static_cast<const double*>(rhs_complex);
-  d.x_fresh = precision_ == TEM_PREC_MIXED ? 1 : 0;
+  d.fp64_inner = precision_ == TEM_PREC_FP64 ? 1 : 0;
   d.nodal = nodal_;
   d.div_nx = make_fastdiv((uint32_t)g.nx);
   d.div_ny = make_fastdiv((uint32_t)g.ny);
@@ -85,7 +85,16 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
 int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
   const int ns = (int)slots_h_.size();
   if (ns == 0) return TEM_EINVAL;
-  // decomposition
+  // decomposition: the z chunk is the longest of 64/32/16/8 planes that still gives
+  // every SM (152) at least 8 stencil CTAs over the whole batch
+  {
+    int64_t cols = 0;
+    for (auto& d : slots_h_) cols += (int64_t)((d.g.nx + TX - 1) / TX) * ((d.g.ny + TY - 1) / TY);
+    int maxnz = 1;
+    for (auto& d : slots_h_) maxnz = std::max(maxnz, d.g.nz);
+    zchunk_ = 64;
+    while (zchunk_ > 8 && cols * ((maxnz + zchunk_ - 1) / zchunk_) < 152 * 8) zchunk_ /= 2;
+  }
   int blk_s = 0, blk_u = 0, blk_n = 0, max_part = 0;
   for (auto& d : slots_h_) {
     d.tiles_x = (d.g.nx + TX - 1) / TX;
@@ -93,7 +102,8 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
     d.zchunks = (d.g.nz + zchunk_ - 1) / zchunk_;
     d.nblk_stencil = d.tiles_x * d.tiles_y * d.zchunks;
     const int64_t n = 3 * d.g.ncomp;
-    d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(4096, (n + NT * 8 - 1) / (NT * 8)));
+    const int64_t nu = n + (nodal_ ? d.g.ncomp : 0);
+    d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (nu + NT * 8 - 1) / (NT * 8)));
     d.nblk_nodal = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (d.g.ncomp + NT * 8 - 1) / (NT * 8)));
     d.blk_stencil0 = blk_s;
     d.blk_update0 = blk_u;
@@ -101,7 +111,7 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
     blk_s += d.nblk_stencil;
     blk_u += d.nblk_update;
     blk_n += d.nblk_nodal;
-    max_part = std::max(max_part, std::max(d.nblk_stencil, d.nblk_nodal) * 4);
+    max_part = std::max(max_part, std::max(d.nblk_stencil, std::max(d.nblk_update, d.nblk_nodal)) * 4);
   }
   nblk_stencil_ = blk_s;
   nblk_update_ = blk_u;
@@ -137,16 +147,10 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
   TEM_CUDA_TRY(cudaMemcpyAsync(map_d_.ptr, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st));
   TEM_CUDA_TRY(cudaMemsetAsync(ticket_d_.ptr, 0, ns * sizeof(unsigned), st));
   TEM_CUDA_TRY(cudaMemsetAsync(counters_d_.ptr, 0, 2 * sizeof(int), st));
-  // zero the vectors the first passes read before writing (x64, directions)
+  // zero every vector: boundary entries must read as 0 and are never written
   for (auto& d : slots_h_) {
-    const size_t n = 3 * (size_t)d.g.ncomp;
-    TEM_CUDA_TRY(cudaMemsetAsync(d.x64[0], 0, n * 16, st));
-    if (d.x64[1] != d.x64[0]) TEM_CUDA_TRY(cudaMemsetAsync(d.x64[1], 0, n * 16, st));
-    const size_t es = precision_ == TEM_PREC_FP64 ? 16 : 8;
-    TEM_CUDA_TRY(cudaMemsetAsync(d.p0, 0, n * es, st));
-    TEM_CUDA_TRY(cudaMemsetAsync(d.p1, 0, n * es, st));
-    TEM_CUDA_TRY(cudaMemsetAsync(d.psi, 0, (size_t)d.g.ncomp * es, st));
-    if (d.x != d.x64[0]) TEM_CUDA_TRY(cudaMemsetAsync(d.x, 0, n * es, st));
+    const size_t bytes = slot_vector_bytes(d.g.ncomp, precision_);
+    TEM_CUDA_TRY(cudaMemsetAsync(d.x64[0], 0, bytes, st));
   }
   if (!counters_h_) TEM_CUDA_TRY(cudaHostAlloc(&counters_h_, 2 * sizeof(int), cudaHostAllocDefault));
   return TEM_OK;
@@ -191,6 +195,7 @@ int Batch::launch_update(cudaStream_t st) {
 }
 
 int Batch::launch_nodal(cudaStream_t st, int init_only) {
+  if (!nodal_) return TEM_OK;
   BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
   if (precision_ == TEM_PREC_FP64)
     k_cocg_nodal<double><<<nblk_nodal_, NT, 0, st>>>(A, init_only);
@@ -206,6 +211,8 @@ int Batch::launch_iteration(cudaStream_t st) {
   TEM_TRY(launch_update(st));
   return launch_nodal(st, 0);
 }
+
+int Batch::launches_per_iteration() const { return nodal_ ? 3 : 2; }
 
 int Batch::launch_residual(cudaStream_t st) {
   BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
@@ -241,7 +248,7 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
     if (counters_h_[0] > 0) {
       for (int it = 0; it < every; ++it) {
         TEM_TRY(launch_iteration(st));
-        launches += 3;
+        launches += launches_per_iteration();
       }
     }
     // slots whose inner solve ended take their FP64 outer step (the others skip it),

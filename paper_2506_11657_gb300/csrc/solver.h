@@ -7,13 +7,9 @@ namespace tem {
 
 // Vectors of one slot (pointers into a batch-owned allocation).
 struct SlotVectors {
-  void* x64[2];
-  void* inner_x;   // MIXED: FP32 correction; FP64: == x64[0]
-  void* r;
-  void* psi;
-  void* p0;
-  void* p1;
-  void* q;
+  void* x64[2];                                   // FP64 iterate (double-buffered)
+  void* x; void* w; void* a0; void* a1; void* q;  // inner edge vectors
+  void* xn; void* psi; void* b0; void* b1; void* cn;  // inner nodal vectors
 };
 
 // Per-slot bytes of the vectors for one grid with `ncomp` entries per direction.
@@ -49,6 +45,7 @@ class Batch {
   int nodal_blocks() const { return nblk_nodal_; }
   // launch one (stencil, update) pair or one residual pass for all slots (bench / profiling)
   int launch_iteration(cudaStream_t st);
+  int launches_per_iteration() const;
   int launch_stencil(cudaStream_t st);
   int launch_update(cudaStream_t st);
   int launch_nodal(cudaStream_t st, int init_only);

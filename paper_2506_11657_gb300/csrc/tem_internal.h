@@ -63,6 +63,8 @@ struct GridView {
   const double* Sx; const double* Sy; const double* Sz;
   const float* Lxf; const float* Lyf; const float* Lzf;
   const float* Sxf; const float* Syf; const float* Szf;
+  const double* Rx; const double* Ry; const double* Rz;   // 1 / L
+  const float* Rxf; const float* Ryf; const float* Rzf;
   const double* Me;         // [3][ncomp] lumped edge mass, 0 on boundary/padding entries
   const float* Mef;         // FP32 copy
   const double* Wn;         // [ncomp] per node: sum over its edges of M_e / L_e^2 (0 on boundary nodes)
@@ -124,11 +126,15 @@ __host__ __device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) 
 struct SlotDesc {
   GridView g;
   double xi_re, xi_im;      // shift
-  void* x;                  // solution (T)
-  void* r;                  // residual (T)
-  void* psi;                // nodal correction D_n^{-1} G^T r (T, one per node)
-  void* p0; void* p1;       // search directions, double-buffered (T)
-  void* q;                  // A p (T)
+  // inner COCG vectors (precision T): edge part and nodal part of the iterate and directions
+  void* x;                  // edge part of the correction
+  void* w;                  // D^{-1} r, the Jacobi-scaled residual (r = D w is rebuilt where needed)
+  void* a0; void* a1;       // edge part of the search direction, double-buffered
+  void* q;                  // A p
+  void* xn;                 // nodal part of the correction (x = x_e + G x_n)
+  void* psi;                // D_n^{-1} G^T r
+  void* b0; void* b1;       // nodal part of the search direction, double-buffered
+  void* cn;                 // G^T of the inner right-hand side, s xi G^T M x64 (set when a solve starts)
   int tiles_x, tiles_y, zchunks;  // stencil decomposition
   int nblk_stencil;         // tiles_x*tiles_y*zchunks
   int nblk_update;          // blocks of the update pass
@@ -140,31 +146,32 @@ struct SlotDesc {
   // defect correction (FP64 outer loop)
   const double* f;          // right-hand side, real, edge layout (FP64)
   const double* rhs_c;      // complex right-hand side (adjoint), or NULL
-  void* x64[2];             // FP64 iterate, double-buffered by the residual pass (MIXED) / x64[0] only (FP64)
-  int x_fresh;              // 1: inner x is a correction starting at 0 (MIXED); 0: inner x is x64 (FP64)
+  void* x64[2];             // FP64 iterate, double-buffered by the residual pass
   int nodal;                // 1: preconditioner with the nodal-gradient correction; 0: Jacobi only
+  int fp64_inner;           // 1: inner sweeps in FP64 (aim at the final tolerance directly)
 };
 
 struct SlotScalars {
   double rho_re, rho_im;    // (r, z) of the current iterate
   double alpha_re, alpha_im;
   double beta_re, beta_im;
+  double rhoe_re, rhoe_im;  // edge part r^T D^{-1} r, from the update (or residual) pass
   double rr;                // ||r||^2 (recursive)
   double bb;                // ||b||^2 of this solve's right-hand side
-  double tol2;              // stop when rr <= tol2 * bb
+  double tol2;              // stop when rr <= tol2
   int32_t active;           // 1 while iterating
   int32_t pending;          // 1 after the residual pass armed an inner solve that the nodal pass has not started
   int32_t iters;
   int32_t max_iter;
   int32_t status;           // TEM_OK / TEM_ENOCONV / TEM_EBREAKDOWN
-  int32_t parity;           // which p buffer holds the current direction
+  int32_t parity;           // which direction buffer holds the current direction
   int32_t xcur;             // which x64 buffer holds the current FP64 iterate
   // outer (FP64 residual) loop
   double ff;                // ||f||^2
   double tol_outer2;        // stop when ||f - A x||^2 <= tol_outer2 (= tol^2 ||f||^2)
   double inner_rel2;        // inner solves stop at ||r_inner||^2 <= inner_rel2 * ||r_start||^2
   double rr64;              // last FP64 residual norm^2
-  double scale;             // inner right-hand side = scale * r64 (MIXED)
+  double scale;             // inner right-hand side = scale * r64
   double inv_scale_prev;    // correction of the last inner solve = inv_scale_prev * delta
   int32_t outer;            // outer steps taken
   int32_t max_outer;

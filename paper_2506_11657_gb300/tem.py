@@ -77,7 +77,7 @@ def lib():
     L.tem_launch_count.argtypes = []
     L.tem_launch_count.restype = C.c_int64
     L.tem_profile_passes.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, C.c_int32,
-                                     C.c_int32, C.c_void_p, _dp, _dp]
+                                     C.c_int32, C.c_int32, C.c_void_p, _dp, _dp]
     _lib = L
     return L
 
@@ -263,7 +263,8 @@ def launch_count() -> int:
     return int(lib().tem_launch_count())
 
 
-def profile_passes(grid: Grid, loop_xy, z_loop, shifts, precision=PREC_MIXED, n_iter=20, current=1.0, stream=None):
+def profile_passes(grid: Grid, loop_xy, z_loop, shifts, precision=PREC_MIXED, n_iter=20, current=1.0, stream=None,
+                   precond=PRECOND_AUTO):
     """Average CUDA-event time (ms) of the stencil, update and FP64 residual passes, and the
     interior edges x shifts one launch processes (tem_profile_passes)."""
     loop = _f64(loop_xy).reshape(-1, 2)
@@ -272,6 +273,7 @@ def profile_passes(grid: Grid, loop_xy, z_loop, shifts, precision=PREC_MIXED, n_
     ms = np.zeros(4)
     units = np.zeros(1)
     _check(lib().tem_profile_passes(grid.handle, _ptr(loop), len(loop), float(z_loop), float(current), _ptr(xi),
-                                    len(shifts), int(precision), int(n_iter), _stream(stream), _ptr(ms), _ptr(units)),
+                                    len(shifts), int(precision), int(precond), int(n_iter), _stream(stream), _ptr(ms),
+                                    _ptr(units)),
            "tem_profile_passes")
     return {"stencil_ms": ms[0], "update_ms": ms[1], "residual_ms": ms[2], "nodal_ms": ms[3], "units": units[0]}
