@@ -33,7 +33,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOADS = {"randblock128": 128, "randblock64": 64}
+WORKLOADS = {"randblock128": 128, "randblock96": 96, "randblock64": 64}
 METRIC = "TEM forward models/s at 128^3 (mixed precision, FP64 residual 1e-12)"
 UNIT = "models/s"
 HBM_FALLBACK_GBS = 6800.0

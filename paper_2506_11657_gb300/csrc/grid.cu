@@ -121,6 +121,31 @@ __global__ void k_node_weight(int nx, int ny, int nz, const double* hx, const do
   }
 }
 
+// diag(K) per edge (Sec. 2.2: K = C^T diag(L*/(mu0 A)) C, so K_ee = L_e^2 sum_{f ni e} L*_f/(mu0 A_f));
+// 0 on boundary and padding entries.
+__global__ void k_diagK(int nx, int ny, int nz, const double* L, const double* S, double* dK, float* dKf) {
+  const int64_t ncomp = (int64_t)nx * ny * nz;
+  const double* Lx = L; const double* Ly = L + nx; const double* Lz = L + nx + ny;
+  const double* Sx = S; const double* Sy = S + nx; const double* Sz = S + nx + ny;
+  const double im = 1.0 / TEM_MU0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * ncomp; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = int(e / ncomp);
+    const int64_t r = e - c * ncomp;
+    const int i = int(r % nx);
+    const int64_t r2 = r / nx;
+    const int j = int(r2 % ny), k = int(r2 / ny);
+    double v = 0.0;
+    if (c == 0 && j > 0 && k > 0)
+      v = Lx[i] * im * (Sz[k] * (1.0 / Ly[j] + 1.0 / Ly[j - 1]) + Sy[j] * (1.0 / Lz[k] + 1.0 / Lz[k - 1]));
+    if (c == 1 && i > 0 && k > 0)
+      v = Ly[j] * im * (Sz[k] * (1.0 / Lx[i] + 1.0 / Lx[i - 1]) + Sx[i] * (1.0 / Lz[k] + 1.0 / Lz[k - 1]));
+    if (c == 2 && i > 0 && j > 0)
+      v = Lz[k] * im * (Sx[i] * (1.0 / Ly[j] + 1.0 / Ly[j - 1]) + Sy[j] * (1.0 / Lx[i] + 1.0 / Lx[i - 1]));
+    dK[e] = v;
+    dKf[e] = float(v);
+  }
+}
+
 static bool finite_positive(const double* a, int64_t n) {
   for (int64_t q = 0; q < n; ++q)
     if (!(std::isfinite(a[q]) && a[q] > 0.0)) return false;
@@ -152,10 +177,10 @@ static int upload_sigma(tem_grid* g, const double* sigma, cudaStream_t st) {
   if (!sigma || !finite_positive(sigma, ncell)) return TEM_EINVAL;
   g->sigma.assign(sigma, sigma + ncell);
   TEM_CUDA_TRY(cudaMemcpyAsync(g->sig.ptr, sigma, ncell * sizeof(double), cudaMemcpyHostToDevice, st));
-  // layout: Me (3n doubles), Wn (n doubles), Mef (3n floats), Wnf (n floats) -- every block aligned
+  // layout: Me (3n), Wn (n), dK (3n) doubles, then Mef (3n), Wnf (n), dKf (3n) floats
   double* Me = g->me.as<double>();
   double* Wn = Me + 3 * ncell;
-  float* Mef = reinterpret_cast<float*>(Wn + ncell);
+  float* Mef = reinterpret_cast<float*>(Wn + 4 * ncell);
   float* Wnf = Mef + 3 * ncell;
   const double* geo = g->geo.as<double>();
   const int nx = g->v.nx, ny = g->v.ny, nz = g->v.nz;
@@ -248,7 +273,7 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   put(nx + ny, g->hz);
   for (int64_t q = 0; q < 9 * n1; ++q) geof[q] = float(geo[q]);
   int rc = g->geo.alloc(9 * n1 * (sizeof(double) + sizeof(float)), st);
-  if (rc == TEM_OK) rc = g->me.alloc(4 * ncell * (sizeof(double) + sizeof(float)), st);
+  if (rc == TEM_OK) rc = g->me.alloc(7 * ncell * (sizeof(double) + sizeof(float)), st);
   if (rc == TEM_OK) rc = g->sig.alloc(ncell * sizeof(double), st);
   if (rc != TEM_OK) {
     delete g;
@@ -275,8 +300,21 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   v.Rxf = gf + 6 * n1; v.Ryf = gf + 6 * n1 + nx; v.Rzf = gf + 6 * n1 + nx + ny;
   v.Me = g->me.as<double>();
   v.Wn = v.Me + 3 * ncell;
-  v.Mef = reinterpret_cast<const float*>(v.Wn + ncell);
+  v.dK = v.Wn + ncell;
+  v.Mef = reinterpret_cast<const float*>(v.dK + 3 * ncell);
   v.Wnf = v.Mef + 3 * ncell;
+  v.dKf = v.Wnf + ncell;
+  {
+    double* dK = const_cast<double*>(v.dK);
+    float* dKf = const_cast<float*>(v.dKf);
+    k_diagK<<<(int)std::min<int64_t>((3 * ncell + 255) / 256, 152 * 32), 256, 0, st>>>(
+        int(nx), int(ny), int(nz), gd, gd + 3 * n1, dK, dKf);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) {
+      delete g;
+      return TEM_ECUDA;
+    }
+  }
   rc = upload_sigma(g, sigma, st);
   if (rc == TEM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = TEM_ECUDA;
   if (rc != TEM_OK) {

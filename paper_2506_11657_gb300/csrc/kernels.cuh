@@ -61,15 +61,16 @@ template <class T> __device__ __forceinline__ void st(void* base, int64_t idx, C
 // 1-D geometry accessors in the working precision
 template <class T> struct Geo;
 template <> struct Geo<double> {
-  const double *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Rx, *Ry, *Rz, *Me, *Wn;
+  const double *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Rx, *Ry, *Rz, *Me, *Wn, *dK;
   __device__ Geo(const GridView& g)
-      : Lx(g.Lx), Ly(g.Ly), Lz(g.Lz), Sx(g.Sx), Sy(g.Sy), Sz(g.Sz), Rx(g.Rx), Ry(g.Ry), Rz(g.Rz), Me(g.Me), Wn(g.Wn) {}
+      : Lx(g.Lx), Ly(g.Ly), Lz(g.Lz), Sx(g.Sx), Sy(g.Sy), Sz(g.Sz), Rx(g.Rx), Ry(g.Ry), Rz(g.Rz), Me(g.Me), Wn(g.Wn),
+        dK(g.dK) {}
 };
 template <> struct Geo<float> {
-  const float *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Rx, *Ry, *Rz, *Me, *Wn;
+  const float *Lx, *Ly, *Lz, *Sx, *Sy, *Sz, *Rx, *Ry, *Rz, *Me, *Wn, *dK;
   __device__ Geo(const GridView& g)
       : Lx(g.Lxf), Ly(g.Lyf), Lz(g.Lzf), Sx(g.Sxf), Sy(g.Syf), Sz(g.Szf), Rx(g.Rxf), Ry(g.Ryf), Rz(g.Rzf),
-        Me(g.Mef), Wn(g.Wnf) {}
+        Me(g.Mef), Wn(g.Wnf), dK(g.dKf) {}
 };
 
 // Diagonal of K at edge (c, i, j, k) (valid, non-boundary edges only):
@@ -149,17 +150,49 @@ constexpr int PY = TY + 2;
 constexpr int FX = TX + 1;   // face tile (-1 .. TX-1)
 constexpr int FY = TY + 1;
 
+constexpr int ZMAX = 64;     // longest z chunk of a stencil CTA
+
+// The CTA's slice of the x and y geometry, staged once: x for i = i0-1 .. i0+TX, y for
+// j = j0-1 .. j0+TY (zero outside the grid).  z values are uniform over a plane and are
+// read as broadcasts.
+template <class T>
+struct TileGeo {
+  T Lx[PX], Rx[PX], Sx[PX];
+  T Ly[PY], Ry[PY], Sy[PY];
+};
+
 template <class T>
 struct StencilSmem {
   C2<T> P[2][3][PY][PX];
   C2<T> F[3][FY][FX];
+  TileGeo<T> geo;
   double red[NT / 32 * 4];
 };
+
+template <class T>
+__device__ __forceinline__ void stage_geometry(TileGeo<T>& tg, const Geo<T>& G, const GridView& g,
+                                               int i0, int j0, int k0, int k1) {
+  for (int t = threadIdx.x; t < PX; t += NT) {
+    const int i = i0 - 1 + t;
+    const bool in = i >= 0 && i < g.nx;
+    tg.Lx[t] = in ? G.Lx[i] : T(0);
+    tg.Rx[t] = in ? G.Rx[i] : T(0);
+    tg.Sx[t] = in ? G.Sx[i] : T(0);
+  }
+  for (int t = threadIdx.x; t < PY; t += NT) {
+    const int j = j0 - 1 + t;
+    const bool in = j >= 0 && j < g.ny;
+    tg.Ly[t] = in ? G.Ly[j] : T(0);
+    tg.Ry[t] = in ? G.Ry[j] : T(0);
+    tg.Sy[t] = in ? G.Sy[j] : T(0);
+  }
+}
 
 // Load plane k of the input into buffer b through the policy's point loader.
 template <class T, class Pol>
 __device__ __forceinline__ void load_plane(StencilSmem<T>& sm, int b, int k, int i0, int j0,
                                            const GridView& g, Pol& pol, bool own_plane) {
+#pragma unroll 1
   for (int t = threadIdx.x; t < 3 * PY * PX; t += NT) {
     const int c = t / (PY * PX);
     const int r = t - c * (PY * PX);
@@ -175,17 +208,19 @@ __device__ __forceinline__ void load_plane(StencilSmem<T>& sm, int b, int k, int
   }
 }
 
-// Faces of plane k (buffer bk) using plane k+1 (buffer bk1), for the tile plus its -1 halo.
+// Faces of plane k (buffer bk) using plane k+1 (buffer bk1), for the tile plus its -1 halo;
+// rLz = 1/Lz_k, sZ = Sz_k / mu0.
 template <class T>
-__device__ __forceinline__ void compute_faces(StencilSmem<T>& sm, int bk, int bk1, int k, int i0, int j0,
-                                              const GridView& g, const Geo<T>& G) {
+__device__ __forceinline__ void compute_faces(StencilSmem<T>& sm, int bk, int bk1, T rLz, T sZ, int i0, int j0,
+                                              const GridView& g) {
   const T inv_mu0 = T(1.0 / TEM_MU0);
+  const TileGeo<T>& tg = sm.geo;
   for (int t = threadIdx.x; t < FY * FX; t += NT) {
     const int jj = t / FX, ii = t - jj * FX;
     const int i = i0 - 1 + ii, j = j0 - 1 + jj;
     C2<T> fx = czero<T>(), fy = czero<T>(), fz = czero<T>();
     if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
-      const T rLx = G.Rx[i], rLy = G.Ry[j], rLz = G.Rz[k];
+      const T rLx = tg.Rx[ii], rLy = tg.Ry[jj];
       // plane-k values around (ii, jj)
       const C2<T> px = sm.P[bk][0][jj][ii], py = sm.P[bk][1][jj][ii], pz = sm.P[bk][2][jj][ii];
       const C2<T> pz_j1 = sm.P[bk][2][jj + 1][ii];
@@ -194,9 +229,9 @@ __device__ __forceinline__ void compute_faces(StencilSmem<T>& sm, int bk, int bk
       const C2<T> py_i1 = sm.P[bk][1][jj][ii + 1];
       const C2<T> px_k1 = sm.P[bk1][0][jj][ii];
       const C2<T> py_k1 = sm.P[bk1][1][jj][ii];
-      fx = (G.Sx[i] * inv_mu0) * (rLz * (py - py_k1) + rLy * (pz_j1 - pz));
-      fy = (G.Sy[j] * inv_mu0) * (rLx * (pz - pz_i1) + rLz * (px_k1 - px));
-      fz = (G.Sz[k] * inv_mu0) * (rLy * (px - px_j1) + rLx * (py_i1 - py));
+      fx = (tg.Sx[ii] * inv_mu0) * (rLz * (py - py_k1) + rLy * (pz_j1 - pz));
+      fy = (tg.Sy[jj] * inv_mu0) * (rLx * (pz - pz_i1) + rLz * (px_k1 - px));
+      fz = sZ * (rLy * (px - px_j1) + rLx * (py_i1 - py));
     }
     sm.F[0][jj][ii] = fx;
     sm.F[1][jj][ii] = fy;
@@ -204,27 +239,29 @@ __device__ __forceinline__ void compute_faces(StencilSmem<T>& sm, int bk, int bk
   }
 }
 
-// Own faces F_x, F_y of plane k for thread (a, b), straight from the planes.
+// Own faces F_x, F_y of plane k for the thread at (ii, jj), straight from the planes.
 template <class T>
-__device__ __forceinline__ void own_faces_xy(const StencilSmem<T>& sm, int bk, int bk1, int k, int i, int j,
-                                             int ii, int jj, const GridView& g, const Geo<T>& G,
-                                             C2<T>& fx, C2<T>& fy) {
+__device__ __forceinline__ void own_faces_xy(const StencilSmem<T>& sm, int bk, int bk1, int k, T rLz, int i, int j,
+                                             int ii, int jj, const GridView& g, C2<T>& fx, C2<T>& fy) {
   fx = czero<T>();
   fy = czero<T>();
   if (k < 0 || k >= g.nz || i >= g.nx || j >= g.ny) return;
   const T inv_mu0 = T(1.0 / TEM_MU0);
-  const T rLx = G.Rx[i], rLy = G.Ry[j], rLz = G.Rz[k];
+  const TileGeo<T>& tg = sm.geo;
+  const T rLx = tg.Rx[ii], rLy = tg.Ry[jj];
   const C2<T> px = sm.P[bk][0][jj][ii], py = sm.P[bk][1][jj][ii], pz = sm.P[bk][2][jj][ii];
-  fx = (G.Sx[i] * inv_mu0) * (rLz * (py - sm.P[bk1][1][jj][ii]) + rLy * (sm.P[bk][2][jj + 1][ii] - pz));
-  fy = (G.Sy[j] * inv_mu0) * (rLx * (pz - sm.P[bk][2][jj][ii + 1]) + rLz * (sm.P[bk1][0][jj][ii] - px));
+  fx = (tg.Sx[ii] * inv_mu0) * (rLz * (py - sm.P[bk1][1][jj][ii]) + rLy * (sm.P[bk][2][jj + 1][ii] - pz));
+  fy = (tg.Sy[jj] * inv_mu0) * (rLx * (pz - sm.P[bk][2][jj][ii + 1]) + rLz * (sm.P[bk1][0][jj][ii] - px));
 }
 
 // The z-marching stencil: for every own valid edge of planes [k0, k1) calls
-// pol.edge(c, idx, i, j, k, p_e, (Kp)_e).  Invalid own edges get pol.edge_invalid(idx).
+// pol.edge(c, idx, i, j, k, p_e, (Kp)_e), after pol.node(n, i, j, k, tg, ii, jj, kz) for its
+// node; invalid own edges get pol.edge_invalid(idx).
 template <class T, class Pol>
 __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView& g, Pol& pol,
                                               int i0, int j0, int k0, int k1) {
   const Geo<T> G(g);
+  stage_geometry<T>(sm.geo, G, g, i0, j0, k0, k1);
   const int a = threadIdx.x % TX, b = threadIdx.x / TX;
   const int i = i0 + a, j = j0 + b;
   const int ii = a + 1, jj = b + 1;
@@ -233,34 +270,37 @@ __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView
   load_plane<T>(sm, 1, k0, i0, j0, g, pol, true);
   __syncthreads();
   C2<T> fxm, fym;  // F_x, F_y of plane k-1 at (i, j)
-  own_faces_xy<T>(sm, 0, 1, k0 - 1, i, j, ii, jj, g, G, fxm, fym);
+  own_faces_xy<T>(sm, 0, 1, k0 - 1, k0 > 0 ? G.Rz[k0 - 1] : T(0), i, j, ii, jj, g, fxm, fym);
   int bk = 1;  // buffer of plane k
+#pragma unroll 1
   for (int k = k0; k < k1; ++k) {
     const int bk1 = bk ^ 1;
+    const T lz = G.Lz[k], rz = G.Rz[k], szm = G.Sz[k] * T(1.0 / TEM_MU0);
     __syncthreads();  // buffer bk1 (plane k-1) and F are free
     load_plane<T>(sm, bk1, k + 1, i0, j0, g, pol, k + 1 < k1);
     __syncthreads();
-    compute_faces<T>(sm, bk, bk1, k, i0, j0, g, G);
+    compute_faces<T>(sm, bk, bk1, rz, szm, i0, j0, g);
     __syncthreads();
     if (i < g.nx && j < g.ny) {
+      const TileGeo<T>& tg = sm.geo;
       const int64_t base = i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
-      pol.node(base, i, j, k);
+      pol.node(base, i, j, k, tg.Rx[ii], tg.Ry[jj], rz);
       const C2<T> fx = sm.F[0][jj][ii], fy = sm.F[1][jj][ii], fz = sm.F[2][jj][ii];
       // x-edge
       if (edge_valid(0, i, j, k)) {
-        const C2<T> kp = G.Lx[i] * ((fz - sm.F[2][jj - 1][ii]) - (fy - fym));
+        const C2<T> kp = tg.Lx[ii] * ((fz - sm.F[2][jj - 1][ii]) - (fy - fym));
         pol.edge(0, base, i, j, k, sm.P[bk][0][jj][ii], kp);
       } else {
         pol.edge_invalid(base);
       }
       if (edge_valid(1, i, j, k)) {
-        const C2<T> kp = G.Ly[j] * ((fx - fxm) - (fz - sm.F[2][jj][ii - 1]));
+        const C2<T> kp = tg.Ly[jj] * ((fx - fxm) - (fz - sm.F[2][jj][ii - 1]));
         pol.edge(1, g.ncomp + base, i, j, k, sm.P[bk][1][jj][ii], kp);
       } else {
         pol.edge_invalid(g.ncomp + base);
       }
       if (edge_valid(2, i, j, k)) {
-        const C2<T> kp = G.Lz[k] * ((fy - sm.F[1][jj][ii - 1]) - (fx - sm.F[0][jj - 1][ii]));
+        const C2<T> kp = lz * ((fy - sm.F[1][jj][ii - 1]) - (fx - sm.F[0][jj - 1][ii]));
         pol.edge(2, 2 * g.ncomp + base, i, j, k, sm.P[bk][2][jj][ii], kp);
       } else {
         pol.edge_invalid(2 * g.ncomp + base);
@@ -310,8 +350,8 @@ __device__ __forceinline__ void tile_of(const SlotDesc& d, int lb, int zchunk, i
 // and K never acts on the large gradient part: in FP32 the rounding of a large
 // gradient would otherwise not be annihilated by K.
 template <class T>
-__device__ __forceinline__ C2<T> jacobi_D(const Geo<T>& G, int c, int i, int j, int k, int64_t idx, C2<T> xi) {
-  return C2<T>(diagK<T>(G, c, i, j, k), T(0)) - (G.Me[idx] * xi);
+__device__ __forceinline__ C2<T> jacobi_D(const Geo<T>& G, int, int, int, int, int64_t idx, C2<T> xi) {
+  return C2<T>(G.dK[idx], T(0)) - (G.Me[idx] * xi);
 }
 
 // (G b)_e for edge (c, i, j, k) from nodal values; nodes at index n (boundary) hold 0.
@@ -361,16 +401,16 @@ struct CocgStencilPol {
     if (use_beta) v = v + cmul(beta, ld<T>(bold, n));
     return v;
   }
-  __device__ void node(int64_t n, int i, int j, int k) {   // once per own node, before its edges
+  __device__ void node(int64_t n, int i, int j, int k, T rx, T ry, T rz) {   // once per own node
     if (!psi) return;
     const C2<T> b0 = bval(n);
     st<T>(bnew, n, b0);
     const C2<T> bx = i + 1 < g->nx ? bval(n + 1) : czero<T>();
     const C2<T> by = j + 1 < g->ny ? bval(n + g->nx) : czero<T>();
     const C2<T> bz = k + 1 < g->nz ? bval(n + (int64_t)g->nx * g->ny) : czero<T>();
-    gb[0] = G.Rx[i] * (bx - b0);
-    gb[1] = G.Ry[j] * (by - b0);
-    gb[2] = G.Rz[k] * (bz - b0);
+    gb[0] = rx * (bx - b0);
+    gb[1] = ry * (by - b0);
+    gb[2] = rz * (bz - b0);
   }
   __device__ void edge(int c, int64_t idx, int, int, int, C2<T> a, C2<T> ka) {
     const C2<T> p = psi ? a + gb[c] : a;
@@ -382,12 +422,12 @@ struct CocgStencilPol {
 };
 
 template <class T>
-__global__ void __launch_bounds__(NT) k_cocg_stencil(BatchArgs A) {
+__global__ void __launch_bounds__(NT, 3) k_cocg_stencil(BatchArgs A) {
   __shared__ StencilSmem<T> sm;
   const int slot = A.blk2slot[blockIdx.x];
   SlotScalars* S = A.sc + slot;
   if (!S->active) return;
-  const SlotDesc d = A.slots[slot];
+  const SlotDesc& d = A.slots[slot];
   const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
   tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
@@ -460,7 +500,8 @@ __device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, 
 }
 
 // ---------- pass B: x += alpha a, x_n += alpha b, r = D w - alpha q, w = r / D; (r, D^-1 r), ||r||
-// Entries [0, 3n) are edges, [3n, 4n) nodes of the slot.
+// A stream over the slot's entries [0, 3n) edges, [3n, 4n) nodes; boundary edges have
+// diag(K) = 0 and are left alone.
 template <class T>
 __global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
   __shared__ double red[NT / 32 * 4];
@@ -469,43 +510,40 @@ __global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
   if (!S->active) return;
   const SlotDesc& d = A.slots[slot];
   const GridView& g = d.g;
-  const Geo<T> G(g);
   const int lb = blockIdx.x - d.blk_update0;
   const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
   const C2<T> xi(T(d.xi_re), T(d.xi_im));
   const bool first = S->iters == 0;                 // the correction starts at 0
   const void* a = S->parity ? d.a0 : d.a1;          // the direction written by pass A
   const void* b = S->parity ? d.b0 : d.b1;
-  const uint32_t ne = (uint32_t)(3 * g.ncomp);
-  const uint32_t n = ne + (d.nodal ? (uint32_t)g.ncomp : 0u);
-  const uint32_t per = (n + d.nblk_update - 1) / d.nblk_update;
-  const uint32_t e0 = (uint32_t)lb * per, e1 = min(n, e0 + per);
+  const T* dK = Geo<T>(g).dK;
+  const T* Me = Geo<T>(g).Me;
+  const int64_t ne = 3 * g.ncomp;
+  const int64_t n = ne + (d.nodal ? g.ncomp : 0);
+  const int64_t per = (n + d.nblk_update - 1) / d.nblk_update;
+  const int64_t e0 = (int64_t)lb * per, e1 = min(n, e0 + per);
   C2<T> rz = czero<T>();
   T rr = T(0);
-  for (uint32_t e = e0 + threadIdx.x; e < e1; e += NT) {
-    if (e >= ne) {  // nodal part of the correction
-      const uint32_t m = e - ne;
-      C2<T> xv = cmul(alpha, ld<T>(b, m));
-      if (!first) xv = xv + ld<T>(d.xn, m);
-      st<T>(d.xn, m, xv);
-      continue;
-    }
-    const uint32_t row = fdiv(e, d.div_nx);
-    const int i = int(e - row * (uint32_t)g.nx);
-    const uint32_t c = fdiv(row, d.div_nynz);
-    const uint32_t jk = row - c * (uint32_t)(g.ny * g.nz);
-    const uint32_t k = fdiv(jk, d.div_ny);
-    const int j = int(jk - k * (uint32_t)g.ny);
-    if (!edge_valid(int(c), i, j, int(k))) continue;
-    C2<T> xv = cmul(alpha, ld<T>(a, e));
-    if (!first) xv = xv + ld<T>(d.x, e);
-    st<T>(d.x, e, xv);
-    const C2<T> D = jacobi_D<T>(G, int(c), i, j, int(k), e, xi);
-    const C2<T> r = cmul(D, ld<T>(d.w, e)) - cmul(alpha, ld<T>(d.q, e));
+  const int64_t ee = min(e1, ne);
+#pragma unroll 4
+  for (int64_t e = e0 + threadIdx.x; e < ee; e += NT) {
+    const T dk = dK[e];
+    const C2<T> av = ld<T>(a, e), qv = ld<T>(d.q, e), wv0 = ld<T>(d.w, e);
+    const C2<T> xo = first ? czero<T>() : ld<T>(d.x, e);
+    if (dk == T(0)) continue;
+    st<T>(d.x, e, xo + cmul(alpha, av));
+    const C2<T> D = C2<T>(dk, T(0)) - (Me[e] * xi);
+    const C2<T> r = cmul(D, wv0) - cmul(alpha, qv);
     const C2<T> wv = cdiv(r, D);
     st<T>(d.w, e, wv);
     rz = rz + cmul(r, wv);
     rr += r.re * r.re + r.im * r.im;
+  }
+  for (int64_t e = max(e0, ne) + threadIdx.x; e < e1; e += NT) {  // nodal part of the correction
+    const int64_t m = e - ne;
+    C2<T> xv = cmul(alpha, ld<T>(b, m));
+    if (!first) xv = xv + ld<T>(d.xn, m);
+    st<T>(d.xn, m, xv);
   }
   double v[3] = {double(rz.re), double(rz.im), double(rr)};
   block_sum<3, NT>(v, red);
@@ -565,13 +603,15 @@ __device__ __forceinline__ C2<T> div_Mv(const Geo<T>& G, const GridView& g, cons
          (G.Rz[k - 1] * G.Me[2 * nc + n - sz]) * zm - (G.Rz[k] * G.Me[2 * nc + n]) * zp;
 }
 
-template <class T>
-__global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A, int init_only) {
+// INIT: the pass that starts an armed solve (cn from x64 in FP64, d = 0); otherwise the
+// pass that ends an iteration of an active solve.
+template <class T, bool INIT>
+__global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
   __shared__ double red[NT / 32 * 4];
   const int slot = A.nblk2slot[blockIdx.x];
   SlotScalars* S = A.sc + slot;
-  const bool pend = S->pending != 0;
-  if (!(pend || (S->active && !init_only))) return;
+  const bool pend = INIT;
+  if (INIT ? !S->pending : !S->active) return;
   const SlotDesc& d = A.slots[slot];
   if (!d.nodal) return;
   const GridView& g = d.g;
@@ -594,8 +634,8 @@ __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A, int init_only) {
     C2<T> ps = czero<T>();
     if (i > 0 && j > 0 && k > 0) {
       C2<T> dv;
-      if (pend) {  // start of a solve: cn = s xi G^T M x64 in FP64; d = 0
-        const C2<double> c0 = (sc * 1.0) * cmul(xi64, div_Mv<double, double>(G64, g, x64, nullptr, i, j, int(k), n));
+      if (INIT) {  // start of a solve: cn = s xi G^T M x64 in FP64; d = 0
+        const C2<double> c0 = sc * cmul(xi64, div_Mv<double, double>(G64, g, x64, nullptr, i, j, int(k), n));
         dv = C2<T>(T(c0.re), T(c0.im));
         st<T>(d.cn, n, dv);
       } else {
@@ -657,7 +697,7 @@ struct ResidualPol {
     }
     return x;
   }
-  __device__ void node(int64_t, int, int, int) {}
+  template <class U> __device__ void node(int64_t, int, int, int, U, U, U) {}
   __device__ void edge(int c, int64_t idx, int i, int j, int k, C2<double> xv, C2<double> kx) {
     const C2<double> ax = kx - cmul(xi, Me[idx] * xv);
     const C2<double> b = rhs_c ? ld<double>(rhs_c, idx) : C2<double>(f[idx], 0.0);
@@ -757,7 +797,7 @@ template <class T>
 struct ApplyPol {
   const void* p; void* q; C2<T> xi; const T* Me;
   __device__ C2<T> load(int, int, int, int, int64_t idx, bool) { return ld<T>(p, idx); }
-  __device__ void node(int64_t, int, int, int) {}
+  __device__ void node(int64_t, int, int, int, T, T, T) {}
   __device__ void edge(int, int64_t idx, int, int, int, C2<T> pv, C2<T> kp) {
     st<T>(q, idx, kp - cmul(xi, Me[idx] * pv));
   }

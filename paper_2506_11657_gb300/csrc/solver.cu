@@ -197,10 +197,13 @@ int Batch::launch_update(cudaStream_t st) {
 int Batch::launch_nodal(cudaStream_t st, int init_only) {
   if (!nodal_) return TEM_OK;
   BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
-  if (precision_ == TEM_PREC_FP64)
-    k_cocg_nodal<double><<<nblk_nodal_, NT, 0, st>>>(A, init_only);
-  else
-    k_cocg_nodal<float><<<nblk_nodal_, NT, 0, st>>>(A, init_only);
+  if (precision_ == TEM_PREC_FP64) {
+    if (init_only) k_cocg_nodal<double, true><<<nblk_nodal_, NT, 0, st>>>(A);
+    else k_cocg_nodal<double, false><<<nblk_nodal_, NT, 0, st>>>(A);
+  } else {
+    if (init_only) k_cocg_nodal<float, true><<<nblk_nodal_, NT, 0, st>>>(A);
+    else k_cocg_nodal<float, false><<<nblk_nodal_, NT, 0, st>>>(A);
+  }
   count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;

@@ -69,6 +69,8 @@ struct GridView {
   const float* Mef;         // FP32 copy
   const double* Wn;         // [ncomp] per node: sum over its edges of M_e / L_e^2 (0 on boundary nodes)
   const float* Wnf;         // FP32 copy
+  const double* dK;         // [3][ncomp] diag(K) per edge, 0 on boundary/padding entries
+  const float* dKf;         // FP32 copy
 };
 
 }  // namespace tem
@@ -79,7 +81,7 @@ struct tem_grid {
   double origin[3];
   std::vector<double> sigma;        // host copy (for the adjoint)
   tem::DevBuf geo;                  // packed 1-D arrays
-  tem::DevBuf me;                   // Me (FP64), Mef (FP32), Wn (FP64), Wnf (FP32)
+  tem::DevBuf me;                   // Me, Wn, dK (FP64) then Mef, Wnf, dKf (FP32)
   tem::DevBuf sig;                  // sigma on the device (FP64)
   int device = 0;
 };
