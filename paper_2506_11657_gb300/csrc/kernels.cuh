@@ -188,23 +188,35 @@ __device__ __forceinline__ void stage_geometry(TileGeo<T>& tg, const Geo<T>& G, 
   }
 }
 
-// Load plane k of the input into buffer b through the policy's point loader.
+// Load plane k of the input into buffer b through the policy's point loader.  Each thread
+// owns ceil(3 PY PX / NT) entries; all of its loads are issued before any shared store.
+constexpr int LPT = (3 * PY * PX + NT - 1) / NT;
 template <class T, class Pol>
 __device__ __forceinline__ void load_plane(StencilSmem<T>& sm, int b, int k, int i0, int j0,
                                            const GridView& g, Pol& pol, bool own_plane) {
-#pragma unroll 1
-  for (int t = threadIdx.x; t < 3 * PY * PX; t += NT) {
-    const int c = t / (PY * PX);
-    const int r = t - c * (PY * PX);
-    const int jj = r / PX, ii = r - jj * PX;
-    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
-    C2<T> v = czero<T>();
-    if (k >= 0 && k < g.nz && i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
-      const int64_t idx = (int64_t)c * g.ncomp + i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
-      const bool own = own_plane && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY;
-      v = pol.load(c, i, j, k, idx, own);
+  C2<T> v[LPT];
+  const bool kin = k >= 0 && k < g.nz;
+#pragma unroll
+  for (int u = 0; u < LPT; ++u) {
+    const int t = threadIdx.x + u * NT;
+    v[u] = czero<T>();
+    if (t < 3 * PY * PX && kin) {
+      const int c = t / (PY * PX);
+      const int r = t - c * (PY * PX);
+      const int jj = r / PX, ii = r - jj * PX;
+      const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+      if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
+        const int64_t idx = (int64_t)c * g.ncomp + i + (int64_t)g.nx * (j + (int64_t)g.ny * k);
+        const bool own = own_plane && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY;
+        v[u] = pol.load(c, i, j, k, idx, own);
+      }
     }
-    sm.P[b][c][jj][ii] = v;
+  }
+  C2<T>* P = &sm.P[b][0][0][0];
+#pragma unroll
+  for (int u = 0; u < LPT; ++u) {
+    const int t = threadIdx.x + u * NT;
+    if (t < 3 * PY * PX) P[t] = v[u];
   }
 }
 
@@ -278,6 +290,7 @@ __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView
     const T lz = G.Lz[k], rz = G.Rz[k], szm = G.Sz[k] * T(1.0 / TEM_MU0);
     __syncthreads();  // buffer bk1 (plane k-1) and F are free
     load_plane<T>(sm, bk1, k + 1, i0, j0, g, pol, k + 1 < k1);
+    if (i < g.nx && j < g.ny) pol.prefetch(i + (int64_t)g.nx * (j + (int64_t)g.ny * k), i, j, k);
     __syncthreads();
     compute_faces<T>(sm, bk, bk1, rz, szm, i0, j0, g);
     __syncthreads();
@@ -379,50 +392,65 @@ __device__ __forceinline__ C2<T> grad_edge(const Geo<T>& G, const GridView& g, i
 // ---------------------- pass A: a <- w + beta a, b <- psi + beta b, q <- A (a + G b), (p, q)
 template <class T>
 struct CocgStencilPol {
-  const void* w; const void* aold; void* anew; void* q;
-  const void* psi; const void* bold; void* bnew;   // nodal part (NULL with Jacobi only)
+  typedef typename Vec2<T>::type V;
+  const V* __restrict__ w; const V* __restrict__ aold; V* __restrict__ anew; V* __restrict__ q;
+  const V* __restrict__ psi; const V* __restrict__ bold; V* __restrict__ bnew;  // nodal part (NULL: Jacobi)
+  const T* __restrict__ Me;
   C2<T> beta; bool use_beta;
   C2<T> xi;
-  Geo<T> G;
   const GridView* g;
   C2<T> acc;
-  __device__ CocgStencilPol(const GridView& gv) : G(gv), g(&gv) {}
+  // prefetched nodal values (own node and its +x, +y, +z neighbours) and masses of the own node
+  C2<T> pb[4], po[4];
+  T me[3];
+  C2<T> gb[3];
+  __device__ CocgStencilPol(const GridView& gv) : g(&gv) {}
+  __device__ static C2<T> L(const V* p, int64_t i) { const V v = __ldg(p + i); return C2<T>(v.x, v.y); }
+  __device__ static void S(V* p, int64_t i, C2<T> a) { V v; v.x = a.re; v.y = a.im; p[i] = v; }
   __device__ C2<T> load(int c, int i, int j, int k, int64_t idx, bool own) {
     if (!edge_valid(c, i, j, k)) return czero<T>();  // boundary: a stays 0 (buffers start zeroed)
-    C2<T> v = ld<T>(w, idx);
-    if (use_beta) v = v + cmul(beta, ld<T>(aold, idx));
-    if (own) st<T>(anew, idx, v);
+    C2<T> v = L(w, idx);
+    if (use_beta) v = v + cmul(beta, L(aold, idx));
+    if (own) S(anew, idx, v);
     return v;
   }
-  // (G b) on the three edges leaving the thread's own node of the current plane
-  C2<T> gb[3];
-  __device__ C2<T> bval(int64_t n) const {
-    C2<T> v = ld<T>(psi, n);
-    if (use_beta) v = v + cmul(beta, ld<T>(bold, n));
-    return v;
-  }
-  __device__ void node(int64_t n, int i, int j, int k, T rx, T ry, T rz) {   // once per own node
+  // issue the loads the edges of node n will need, before the face phase
+  __device__ void prefetch(int64_t n, int i, int j, int k) {
+    const int64_t nc = g->ncomp;
+    me[0] = __ldg(Me + n);
+    me[1] = __ldg(Me + nc + n);
+    me[2] = __ldg(Me + 2 * nc + n);
     if (!psi) return;
-    const C2<T> b0 = bval(n);
-    st<T>(bnew, n, b0);
-    const C2<T> bx = i + 1 < g->nx ? bval(n + 1) : czero<T>();
-    const C2<T> by = j + 1 < g->ny ? bval(n + g->nx) : czero<T>();
-    const C2<T> bz = k + 1 < g->nz ? bval(n + (int64_t)g->nx * g->ny) : czero<T>();
-    gb[0] = rx * (bx - b0);
-    gb[1] = ry * (by - b0);
-    gb[2] = rz * (bz - b0);
+    const int64_t nb[4] = {n, n + 1, n + g->nx, n + (int64_t)g->nx * g->ny};
+    const bool in[4] = {true, i + 1 < g->nx, j + 1 < g->ny, k + 1 < g->nz};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pb[u] = in[u] ? L(psi, nb[u]) : czero<T>();
+      po[u] = (in[u] && use_beta) ? L(bold, nb[u]) : czero<T>();
+    }
+  }
+  __device__ void node(int64_t n, int, int, int, T rx, T ry, T rz) {   // once per own node
+    if (!psi) return;
+    C2<T> b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b[u] = use_beta ? pb[u] + cmul(beta, po[u]) : pb[u];
+    S(bnew, n, b[0]);
+    gb[0] = rx * (b[1] - b[0]);
+    gb[1] = ry * (b[2] - b[0]);
+    gb[2] = rz * (b[3] - b[0]);
   }
   __device__ void edge(int c, int64_t idx, int, int, int, C2<T> a, C2<T> ka) {
     const C2<T> p = psi ? a + gb[c] : a;
-    const C2<T> qv = ka - cmul(xi, G.Me[idx] * p);
-    st<T>(q, idx, qv);
+    const C2<T> qv = ka - cmul(xi, me[c] * p);
+    S(q, idx, qv);
     acc = acc + cmul(p, qv);
   }
-  __device__ void edge_invalid(int64_t idx) { st<T>(q, idx, czero<T>()); }
+  __device__ void edge_invalid(int64_t idx) { S(q, idx, czero<T>()); }
 };
 
+// FP32: at least 3 CTAs (24 warps) per SM; FP64 keeps its registers (it is bound by FP64 issue)
 template <class T>
-__global__ void __launch_bounds__(NT, 3) k_cocg_stencil(BatchArgs A) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_cocg_stencil(BatchArgs A) {
   __shared__ StencilSmem<T> sm;
   const int slot = A.blk2slot[blockIdx.x];
   SlotScalars* S = A.sc + slot;
@@ -432,13 +460,15 @@ __global__ void __launch_bounds__(NT, 3) k_cocg_stencil(BatchArgs A) {
   int i0, j0, k0, k1;
   tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
   CocgStencilPol<T> pol(d.g);
-  pol.w = d.w;
-  pol.aold = S->parity ? d.a1 : d.a0;
-  pol.anew = S->parity ? d.a0 : d.a1;
-  pol.psi = d.nodal ? d.psi : nullptr;
-  pol.bold = S->parity ? d.b1 : d.b0;
-  pol.bnew = S->parity ? d.b0 : d.b1;
-  pol.q = d.q;
+  typedef typename Vec2<T>::type V;
+  pol.w = static_cast<const V*>(d.w);
+  pol.aold = static_cast<const V*>(S->parity ? d.a1 : d.a0);
+  pol.anew = static_cast<V*>(S->parity ? d.a0 : d.a1);
+  pol.psi = d.nodal ? static_cast<const V*>(d.psi) : nullptr;
+  pol.bold = static_cast<const V*>(S->parity ? d.b1 : d.b0);
+  pol.bnew = static_cast<V*>(S->parity ? d.b0 : d.b1);
+  pol.q = static_cast<V*>(d.q);
+  pol.Me = Geo<T>(d.g).Me;
   pol.beta = C2<T>(T(S->beta_re), T(S->beta_im));
   pol.use_beta = !(S->beta_re == 0.0 && S->beta_im == 0.0);
   pol.xi = C2<T>(T(d.xi_re), T(d.xi_im));
@@ -479,7 +509,13 @@ __device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, 
   } else if (S->iters >= S->max_iter) {
     S->status = TEM_ENOCONV;
     done = true;
+  } else if (rr >= S->rr_best && S->iters - S->it_best > S->stall_window) {
+    done = true;  // stagnation: end this inner solve; the FP64 outer step restarts from the true residual
   } else {
+    if (rr < S->rr_best) {
+      S->rr_best = rr;
+      S->it_best = S->iters;
+    }
     const double den = S->rho_re * S->rho_re + S->rho_im * S->rho_im;
     if (!(den > 0.0)) {
       S->status = TEM_EBREAKDOWN;
@@ -503,7 +539,7 @@ __device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, 
 // A stream over the slot's entries [0, 3n) edges, [3n, 4n) nodes; boundary edges have
 // diag(K) = 0 and are left alone.
 template <class T>
-__global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(BatchArgs A) {
   __shared__ double red[NT / 32 * 4];
   const int slot = A.ublk2slot[blockIdx.x];
   SlotScalars* S = A.sc + slot;
@@ -516,8 +552,13 @@ __global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
   const bool first = S->iters == 0;                 // the correction starts at 0
   const void* a = S->parity ? d.a0 : d.a1;          // the direction written by pass A
   const void* b = S->parity ? d.b0 : d.b1;
-  const T* dK = Geo<T>(g).dK;
-  const T* Me = Geo<T>(g).Me;
+  typedef typename Vec2<T>::type V;
+  const T* __restrict__ dK = Geo<T>(g).dK;
+  const T* __restrict__ Me = Geo<T>(g).Me;
+  const V* __restrict__ av = static_cast<const V*>(a);
+  const V* __restrict__ qv = static_cast<const V*>(d.q);
+  V* __restrict__ wv = static_cast<V*>(d.w);
+  V* __restrict__ xv = static_cast<V*>(d.x);
   const int64_t ne = 3 * g.ncomp;
   const int64_t n = ne + (d.nodal ? g.ncomp : 0);
   const int64_t per = (n + d.nblk_update - 1) / d.nblk_update;
@@ -525,25 +566,46 @@ __global__ void __launch_bounds__(NT) k_cocg_update(BatchArgs A) {
   C2<T> rz = czero<T>();
   T rr = T(0);
   const int64_t ee = min(e1, ne);
-#pragma unroll 4
-  for (int64_t e = e0 + threadIdx.x; e < ee; e += NT) {
-    const T dk = dK[e];
-    const C2<T> av = ld<T>(a, e), qv = ld<T>(d.q, e), wv0 = ld<T>(d.w, e);
-    const C2<T> xo = first ? czero<T>() : ld<T>(d.x, e);
-    if (dk == T(0)) continue;
-    st<T>(d.x, e, xo + cmul(alpha, av));
-    const C2<T> D = C2<T>(dk, T(0)) - (Me[e] * xi);
-    const C2<T> r = cmul(D, wv0) - cmul(alpha, qv);
-    const C2<T> wv = cdiv(r, D);
-    st<T>(d.w, e, wv);
-    rz = rz + cmul(r, wv);
-    rr += r.re * r.re + r.im * r.im;
+  constexpr int U = 2;
+  for (int64_t base = e0 + threadIdx.x; base < ee; base += (int64_t)NT * U) {
+    T dk[U], me[U];
+    V ar[U], qr[U], wr[U], xr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = base + (int64_t)u * NT;
+      if (e < ee) {
+        dk[u] = __ldg(dK + e);
+        me[u] = __ldg(Me + e);
+        ar[u] = __ldg(av + e);
+        qr[u] = __ldg(qv + e);
+        wr[u] = wv[e];
+        if (!first) xr[u] = xv[e];
+        else { xr[u].x = T(0); xr[u].y = T(0); }
+      } else {
+        dk[u] = T(0);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t e = base + (int64_t)u * NT;
+      if (dk[u] == T(0)) continue;  // boundary entry (or past the range)
+      const C2<T> xn = C2<T>(xr[u].x, xr[u].y) + cmul(alpha, C2<T>(ar[u].x, ar[u].y));
+      V xo; xo.x = xn.re; xo.y = xn.im;
+      xv[e] = xo;
+      const C2<T> D = C2<T>(dk[u], T(0)) - (me[u] * xi);
+      const C2<T> r = cmul(D, C2<T>(wr[u].x, wr[u].y)) - cmul(alpha, C2<T>(qr[u].x, qr[u].y));
+      const C2<T> wn = cdiv(r, D);
+      V wo; wo.x = wn.re; wo.y = wn.im;
+      wv[e] = wo;
+      rz = rz + cmul(r, wn);
+      rr += r.re * r.re + r.im * r.im;
+    }
   }
   for (int64_t e = max(e0, ne) + threadIdx.x; e < e1; e += NT) {  // nodal part of the correction
     const int64_t m = e - ne;
-    C2<T> xv = cmul(alpha, ld<T>(b, m));
-    if (!first) xv = xv + ld<T>(d.xn, m);
-    st<T>(d.xn, m, xv);
+    C2<T> xn = cmul(alpha, ld<T>(b, m));
+    if (!first) xn = xn + ld<T>(d.xn, m);
+    st<T>(d.xn, m, xn);
   }
   double v[3] = {double(rz.re), double(rz.im), double(rr)};
   block_sum<3, NT>(v, red);
@@ -698,6 +760,7 @@ struct ResidualPol {
     return x;
   }
   template <class U> __device__ void node(int64_t, int, int, int, U, U, U) {}
+  __device__ void prefetch(int64_t, int, int, int) {}
   __device__ void edge(int c, int64_t idx, int i, int j, int k, C2<double> xv, C2<double> kx) {
     const C2<double> ax = kx - cmul(xi, Me[idx] * xv);
     const C2<double> b = rhs_c ? ld<double>(rhs_c, idx) : C2<double>(f[idx], 0.0);
@@ -775,6 +838,8 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
     S->tol2 = rel2 * S->bb;
     S->iters = 0;
     S->parity = 0;
+    S->rr_best = S->bb;
+    S->it_best = 0;
     S->inv_scale_prev = 1.0 / sc;
     S->scale = 1.0 / sqrt(tot[0]);
     S->rhoe_re = tot[1];
@@ -798,6 +863,7 @@ struct ApplyPol {
   const void* p; void* q; C2<T> xi; const T* Me;
   __device__ C2<T> load(int, int, int, int, int64_t idx, bool) { return ld<T>(p, idx); }
   __device__ void node(int64_t, int, int, int, T, T, T) {}
+  __device__ void prefetch(int64_t, int, int, int) {}
   __device__ void edge(int, int64_t idx, int, int, int, C2<T> pv, C2<T> kp) {
     st<T>(q, idx, kp - cmul(xi, Me[idx] * pv));
   }

@@ -135,6 +135,7 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
     S.scale = precision_ == TEM_PREC_MIXED ? 1.0 / std::sqrt(ff[q]) : 1.0;
     S.inv_scale_prev = 1.0;
     S.max_outer = opt.max_outer;
+    S.stall_window = 400;
   }
   TEM_TRY(slots_d_.alloc(ns * sizeof(SlotDesc), st));
   TEM_TRY(sc_d_.alloc(ns * sizeof(SlotScalars), st));

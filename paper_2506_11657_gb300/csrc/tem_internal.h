@@ -179,6 +179,9 @@ struct SlotScalars {
   int32_t max_outer;
   int32_t done;             // 1 once the FP64 residual met the tolerance (or the slot failed)
   int32_t total_iters;      // inner iterations summed over outer steps
+  double rr_best;           // smallest recursive ||r||^2 of the current inner solve
+  int32_t it_best;          // iteration that reached it
+  int32_t stall_window;     // end the inner solve after this many iterations without a new best
 };
 
 }  // namespace tem
