@@ -213,6 +213,55 @@ int tem_state_destroy(tem_state* state);
 int tem_apply_operator(const tem_grid* grid, const double* xi, int64_t s,
                        const void* p_dev, void* q_dev, int32_t precision, void* cuda_stream);
 
+/* ---- serving: continuous batching of forward models -------------------------
+ *
+ * A server owns one CUDA stream's worth of device work.  Requests (each a whole
+ * forward model: grid, conductivity, loop, receivers, shifts, weights) are queued
+ * by tem_server_submit, admitted in arrival order when enough slots (one per
+ * shift) are free and their device footprint fits the HBM budget, and then
+ * advanced together: every tem_server_step launches the stencil, update and
+ * nodal passes once per COCG iteration over the shifts of all admitted requests
+ * at once (plus the FP64 residual passes of shifts whose inner solve ended).
+ * A request that arrives while others run is admitted at the next step that has
+ * room; its Krylov state stays on the device until it finishes.  Each shift's
+ * arithmetic (its tiling and the order of its reductions) depends only on its own
+ * grid, so a request's result is bitwise the same alone and in any mix.
+ * Not thread-safe: one host thread drives a server.
+ */
+typedef struct tem_server tem_server;
+
+typedef struct tem_server_options {
+  int64_t hbm_budget_bytes;  /* admit while the footprints of running requests fit (default: 80% of free memory) */
+  int32_t max_slots;         /* shifted systems in flight at once (default 128, at most 1024) */
+  int32_t iters_per_step;    /* COCG iterations per tem_server_step (default 32) */
+  tem_options solver;        /* precision, tolerances, preconditioner (keep_state is ignored) */
+} tem_server_options;
+
+typedef struct tem_request_stats {
+  double submit_s, admit_s, done_s;  /* host steady-clock times (s) */
+  int64_t footprint_bytes;           /* device bytes the request held while running */
+  int32_t status;                    /* TEM_OK, TEM_ENOCONV or TEM_EBREAKDOWN */
+  int32_t max_iters;                 /* largest per-shift COCG iteration count */
+} tem_request_stats;
+
+void tem_server_default_options(tem_server_options* opt);
+int tem_server_create(const tem_server_options* opt, void* cuda_stream, tem_server** out);
+/* Queue one forward model (arguments as for tem_build_grid and tem_forward; all are copied).
+   Errors: TEM_EINVAL for bad input (checked now, on the host). */
+int tem_server_submit(tem_server* srv, const double* hx, int64_t nx, const double* hy, int64_t ny,
+                      const double* hz, int64_t nz, const double* origin, const double* sigma,
+                      const double* loop_xy, int64_t n_vertices, double z_loop, double current,
+                      const double* rx_xyz, int64_t n_rx, const double* xi, const double* c, int64_t s,
+                      int64_t K, int64_t* ticket_out);
+/* One scheduling round: admit what fits, run iters_per_step iterations for every admitted
+   request, finish the requests whose shifts have all converged.  Returns after the round. */
+int tem_server_step(tem_server* srv);
+/* TEM_EBUSY while the request is queued or running; otherwise its status, with
+   dbzdt_out (n_rx*K doubles) and stats written once (the ticket is then released). */
+int tem_server_poll(tem_server* srv, int64_t ticket, double* dbzdt_out, tem_request_stats* stats);
+int tem_server_counts(const tem_server* srv, int64_t* queued, int64_t* running, int64_t* finished);
+int tem_server_destroy(tem_server* srv);
+
 /*
  * tem_apply_operator without any device allocation.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory, such as a

@@ -336,11 +336,10 @@ struct BatchArgs {
   unsigned* ticket;          // [slot]
   int* n_active;             // slots armed or iterating
   int part_stride;           // doubles per slot in part
-  int zchunk;                // planes per stencil CTA
 };
 
-__device__ __forceinline__ void tile_of(const SlotDesc& d, int lb, int zchunk, int nz,
-                                        int& i0, int& j0, int& k0, int& k1) {
+__device__ __forceinline__ void tile_of(const SlotDesc& d, int lb, int nz, int& i0, int& j0, int& k0, int& k1) {
+  const int zchunk = d.zchunk;
   const int tx = lb % d.tiles_x;
   const int r = lb / d.tiles_x;
   const int ty = r % d.tiles_y;
@@ -458,7 +457,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_cocg_stencil(Bat
   const SlotDesc& d = A.slots[slot];
   const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
-  tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
+  tile_of(d, lb, d.g.nz, i0, j0, k0, k1);
   CocgStencilPol<T> pol(d.g);
   typedef typename Vec2<T>::type V;
   pol.w = static_cast<const V*>(d.w);
@@ -785,7 +784,7 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
   const SlotDesc d = A.slots[slot];
   const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
-  tile_of(d, lb, A.zchunk, d.g.nz, i0, j0, k0, k1);
+  tile_of(d, lb, d.g.nz, i0, j0, k0, k1);
   ResidualPol<TI> pol(d.g);
   pol.upd = S->outer > 0;
   pol.xcur = d.x64[S->xcur];

@@ -47,6 +47,20 @@ SlotVectors carve_slot(void* base, int64_t ncomp, int precision) {
   return v;
 }
 
+void decompose_slot(SlotDesc& d, int nodal) {
+  d.tiles_x = (d.g.nx + TX - 1) / TX;
+  d.tiles_y = (d.g.ny + TY - 1) / TY;
+  // the longest z chunk (64/32/16/8 planes) that gives the slot alone 2 CTAs per SM (152 SMs)
+  const int64_t cols = (int64_t)d.tiles_x * d.tiles_y;
+  d.zchunk = 64;
+  while (d.zchunk > 8 && cols * ((d.g.nz + d.zchunk - 1) / d.zchunk) < 2 * 152) d.zchunk /= 2;
+  d.zchunks = (d.g.nz + d.zchunk - 1) / d.zchunk;
+  d.nblk_stencil = d.tiles_x * d.tiles_y * d.zchunks;
+  const int64_t n = 3 * d.g.ncomp + (nodal ? d.g.ncomp : 0);
+  d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (n + NT * 8 - 1) / (NT * 8)));
+  d.nblk_nodal = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (d.g.ncomp + NT * 8 - 1) / (NT * 8)));
+}
+
 Batch::~Batch() {
   if (counters_h_) cudaFreeHost(counters_h_);
 }
@@ -85,26 +99,9 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
 int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
   const int ns = (int)slots_h_.size();
   if (ns == 0) return TEM_EINVAL;
-  // decomposition: the z chunk is the longest of 64/32/16/8 planes that still gives
-  // every SM (152) at least 8 stencil CTAs over the whole batch
-  {
-    int64_t cols = 0;
-    for (auto& d : slots_h_) cols += (int64_t)((d.g.nx + TX - 1) / TX) * ((d.g.ny + TY - 1) / TY);
-    int maxnz = 1;
-    for (auto& d : slots_h_) maxnz = std::max(maxnz, d.g.nz);
-    zchunk_ = 64;
-    while (zchunk_ > 8 && cols * ((maxnz + zchunk_ - 1) / zchunk_) < 152 * 8) zchunk_ /= 2;
-  }
   int blk_s = 0, blk_u = 0, blk_n = 0, max_part = 0;
   for (auto& d : slots_h_) {
-    d.tiles_x = (d.g.nx + TX - 1) / TX;
-    d.tiles_y = (d.g.ny + TY - 1) / TY;
-    d.zchunks = (d.g.nz + zchunk_ - 1) / zchunk_;
-    d.nblk_stencil = d.tiles_x * d.tiles_y * d.zchunks;
-    const int64_t n = 3 * d.g.ncomp;
-    const int64_t nu = n + (nodal_ ? d.g.ncomp : 0);
-    d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (nu + NT * 8 - 1) / (NT * 8)));
-    d.nblk_nodal = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (d.g.ncomp + NT * 8 - 1) / (NT * 8)));
+    decompose_slot(d, nodal_);
     d.blk_stencil0 = blk_s;
     d.blk_update0 = blk_u;
     d.blk_nodal0 = blk_n;
@@ -132,7 +129,7 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
     S.ff = ff[q];
     S.tol_outer2 = opt.tol * opt.tol * ff[q];
     S.inner_rel2 = opt.inner_tol * opt.inner_tol;
-    S.scale = precision_ == TEM_PREC_MIXED ? 1.0 / std::sqrt(ff[q]) : 1.0;
+    S.scale = 1.0 / std::sqrt(ff[q]);
     S.inv_scale_prev = 1.0;
     S.max_outer = opt.max_outer;
     S.stall_window = 400;
@@ -158,7 +155,7 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
 }
 
 static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& map, int nblk_s, int nblk_u,
-                           const DevBuf& part, const DevBuf& ticket, const DevBuf& counters, int stride, int zchunk) {
+                           const DevBuf& part, const DevBuf& ticket, const DevBuf& counters, int stride) {
   BatchArgs A;
   A.slots = slots.as<SlotDesc>();
   A.sc = sc.as<SlotScalars>();
@@ -169,12 +166,11 @@ static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& 
   A.ticket = ticket.as<unsigned>();
   A.n_active = counters.as<int>();
   A.part_stride = stride;
-  A.zchunk = zchunk;
   return A;
 }
 
 int Batch::launch_stencil(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
   if (precision_ == TEM_PREC_FP64)
     k_cocg_stencil<double><<<nblk_stencil_, NT, 0, st>>>(A);
   else
@@ -185,7 +181,7 @@ int Batch::launch_stencil(cudaStream_t st) {
 }
 
 int Batch::launch_update(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
   if (precision_ == TEM_PREC_FP64)
     k_cocg_update<double><<<nblk_update_, NT, 0, st>>>(A);
   else
@@ -197,7 +193,7 @@ int Batch::launch_update(cudaStream_t st) {
 
 int Batch::launch_nodal(cudaStream_t st, int init_only) {
   if (!nodal_) return TEM_OK;
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
   if (precision_ == TEM_PREC_FP64) {
     if (init_only) k_cocg_nodal<double, true><<<nblk_nodal_, NT, 0, st>>>(A);
     else k_cocg_nodal<double, false><<<nblk_nodal_, NT, 0, st>>>(A);
@@ -219,7 +215,7 @@ int Batch::launch_iteration(cudaStream_t st) {
 int Batch::launches_per_iteration() const { return nodal_ ? 3 : 2; }
 
 int Batch::launch_residual(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_, zchunk_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
   int* n_done = counters_d_.as<int>() + 1;
   if (precision_ == TEM_PREC_FP64)
     k_residual<double><<<nblk_stencil_, NT, 0, st>>>(A, n_done);

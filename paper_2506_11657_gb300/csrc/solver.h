@@ -39,7 +39,7 @@ class Batch {
   int nslots() const { return (int)slots_h_.size(); }
   const std::vector<SlotDesc>& slots_host() const { return slots_h_; }
   int precision() const { return precision_; }
-  int zchunk() const { return zchunk_; }
+
   int stencil_blocks() const { return nblk_stencil_; }
   int update_blocks() const { return nblk_update_; }
   int nodal_blocks() const { return nblk_nodal_; }
@@ -54,7 +54,6 @@ class Batch {
  private:
   int precision_;
   int nodal_;
-  int zchunk_ = 32;
   std::vector<SlotDesc> slots_h_;
   std::vector<SlotScalars> sc_h_;
   int nblk_stencil_ = 0, nblk_update_ = 0, nblk_nodal_ = 0;
@@ -65,5 +64,10 @@ class Batch {
 
 // process-wide count of kernels launched by the library
 void count_launch(int n = 1);
+
+// Stencil decomposition of one slot (tiles, z chunk, CTA counts): depends only on the
+// slot's grid, so a slot's arithmetic is the same in any batch.
+void decompose_slot(SlotDesc& d, int nodal);
+constexpr int kMaxBlocksPerSlot = 4096;
 
 }  // namespace tem

@@ -138,6 +138,7 @@ struct SlotDesc {
   void* b0; void* b1;       // nodal part of the search direction, double-buffered
   void* cn;                 // G^T of the inner right-hand side, s xi G^T M x64 (set when a solve starts)
   int tiles_x, tiles_y, zchunks;  // stencil decomposition
+  int zchunk;               // planes per stencil CTA (a function of this slot's grid only)
   int nblk_stencil;         // tiles_x*tiles_y*zchunks
   int nblk_update;          // blocks of the update pass
   int nblk_nodal;           // blocks of the nodal pass

@@ -24,7 +24,8 @@ EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
             "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_adjoint",
             "tem_state_destroy", "tem_apply_operator", "tem_apply_operator_noalloc", "tem_launch_count",
-            "tem_profile_passes"]
+            "tem_profile_passes", "tem_server_default_options", "tem_server_create", "tem_server_submit",
+            "tem_server_step", "tem_server_poll", "tem_server_counts", "tem_server_destroy"]
 
 
 class TEMError(RuntimeError):
@@ -37,6 +38,16 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32),
                 ("keep_state", C.c_int32), ("precond", C.c_int32)]
+
+
+class ServerOptions(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_slots", C.c_int32), ("iters_per_step", C.c_int32),
+                ("solver", Options)]
+
+
+class RequestStats(C.Structure):
+    _fields_ = [("submit_s", C.c_double), ("admit_s", C.c_double), ("done_s", C.c_double),
+                ("footprint_bytes", C.c_int64), ("status", C.c_int32), ("max_iters", C.c_int32)]
 
 
 _lib = None
@@ -74,6 +85,16 @@ def lib():
     L.tem_apply_operator.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
     L.tem_apply_operator_noalloc.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
                                              C.c_void_p]
+    L.tem_server_default_options.argtypes = [C.POINTER(ServerOptions)]
+    L.tem_server_default_options.restype = None
+    L.tem_server_create.argtypes = [C.POINTER(ServerOptions), C.c_void_p, C.POINTER(C.c_void_p)]
+    L.tem_server_submit.argtypes = [C.c_void_p, _dp, C.c_int64, _dp, C.c_int64, _dp, C.c_int64, _dp, _dp, _dp,
+                                    C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, _dp, _dp, C.c_int64,
+                                    C.c_int64, _i64p]
+    L.tem_server_step.argtypes = [C.c_void_p]
+    L.tem_server_poll.argtypes = [C.c_void_p, C.c_int64, _dp, C.POINTER(RequestStats)]
+    L.tem_server_counts.argtypes = [C.c_void_p, _i64p, _i64p, _i64p]
+    L.tem_server_destroy.argtypes = [C.c_void_p]
     L.tem_launch_count.argtypes = []
     L.tem_launch_count.restype = C.c_int64
     L.tem_profile_passes.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, C.c_int32,
@@ -277,3 +298,73 @@ def profile_passes(grid: Grid, loop_xy, z_loop, shifts, precision=PREC_MIXED, n_
                                     _ptr(units)),
            "tem_profile_passes")
     return {"stencil_ms": ms[0], "update_ms": ms[1], "residual_ms": ms[2], "nodal_ms": ms[3], "units": units[0]}
+
+
+class Server:
+    """Continuous-batching server of forward models (tem_server_*)."""
+
+    def __init__(self, hbm_budget_bytes=None, max_slots=None, iters_per_step=None, stream=None, **solver):
+        o = ServerOptions()
+        lib().tem_server_default_options(C.byref(o))
+        if hbm_budget_bytes is not None:
+            o.hbm_budget_bytes = int(hbm_budget_bytes)
+        if max_slots is not None:
+            o.max_slots = int(max_slots)
+        if iters_per_step is not None:
+            o.iters_per_step = int(iters_per_step)
+        base = default_options(**solver) if solver else None
+        if base is not None:
+            o.solver = base
+        if "precision" not in solver:
+            o.solver.precision = PREC_MIXED
+        h = C.c_void_p()
+        _check(lib().tem_server_create(C.byref(o), _stream(stream), C.byref(h)), "tem_server_create")
+        self.handle = h
+        self.shapes = {}
+
+    def submit(self, model, shifts, c):
+        """Queue a workloads.Model with its shifts/weights; returns the ticket."""
+        hx, hy, hz = _f64(model.hx), _f64(model.hy), _f64(model.hz)
+        org, sig = _f64(model.origin), _f64(model.sigma).ravel()
+        loop, rx = _f64(model.loop_xy).reshape(-1, 2), _f64(model.rx).reshape(-1, 3)
+        sh = np.ascontiguousarray(shifts, dtype=np.complex128)
+        cc = np.ascontiguousarray(c, dtype=np.complex128)
+        s, K = cc.shape
+        t = C.c_int64()
+        _check(lib().tem_server_submit(self.handle, _ptr(hx), len(hx), _ptr(hy), len(hy), _ptr(hz), len(hz), _ptr(org),
+                                       _ptr(sig), _ptr(loop), len(loop), float(model.z_loop), float(model.current),
+                                       _ptr(rx), len(rx), _ptr(sh.view(np.float64)), _ptr(cc.view(np.float64).ravel()),
+                                       s, K, C.byref(t)), "tem_server_submit")
+        self.shapes[t.value] = (len(rx), K)
+        return t.value
+
+    def step(self):
+        _check(lib().tem_server_step(self.handle), "tem_server_step")
+
+    def poll(self, ticket):
+        """None while queued/running; else (d, stats dict)."""
+        n_rx, K = self.shapes[ticket]
+        out = np.zeros((n_rx, K))
+        st = RequestStats()
+        rc = lib().tem_server_poll(self.handle, int(ticket), _ptr(out), C.byref(st))
+        if rc == TEM_EBUSY:
+            return None
+        del self.shapes[ticket]
+        stats = {k: getattr(st, k) for k, _ in RequestStats._fields_}
+        return out, stats
+
+    def counts(self):
+        q, r, d = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(lib().tem_server_counts(self.handle, C.byref(q), C.byref(r), C.byref(d)), "tem_server_counts")
+        return q.value, r.value, d.value
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tem_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
