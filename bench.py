@@ -163,6 +163,50 @@ def cpu_oracle_sample(model, shifts, iters_per_shift, n_iter=12):
     return 1.0 / model_s, t2 - t0, desc
 
 
+def run_serving_sample(n_req, stream):
+    """Continuous batching on the first n_req requests of the seeded serving stream (grids of
+    32^3..96^3, 16-20 poles): all arriving at once (capacity), then Poisson arrivals at 1.2x that
+    capacity (latency).  Beside it, the same requests one at a time through tem_forward in FP64."""
+    import torch
+    from paper_2506_11657_gb300 import tem, workloads as W
+    from paper_2506_11657_gb300.serving import PoleCache, run_stream
+    stream_items = W.serving_stream(n_requests=n_req, seed=4)
+    models = [m for _, m in stream_items]
+    poles = PoleCache()
+    for m in models:
+        poles.get(m.t, m.degree)
+    torch.cuda.synchronize()
+    srv = tem.Server(stream=stream)
+    _, sat = run_stream(srv, [(0.0, m) for m in models], poles)
+    cap = sat["models_per_s"]
+    rng = np.random.default_rng(4)
+    arr = np.cumsum(rng.exponential(1.0 / (1.2 * cap), size=len(models)))
+    srv2 = tem.Server(stream=stream)
+    _, lat = run_stream(srv2, [(float(a), m) for a, m in zip(arr, models)], poles)
+    srv.close()
+    srv2.close()
+    # the served mixed form against FP64 one model at a time, on the same quarter of the requests
+    k = max(1, len(models) // 4)
+    srv3 = tem.Server(stream=stream)
+    _, sat_k = run_stream(srv3, [(0.0, m) for m in models[:k]], poles)
+    srv3.close()
+    t0 = time.perf_counter()
+    for m in models[:k]:
+        g = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma, stream=stream)
+        sh, c = poles.get(m.t, m.degree)
+        tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, tem.default_options(precision="fp64"), stream=stream)
+        g.close()
+    torch.cuda.synchronize()
+    fp64_rate = k / (time.perf_counter() - t0)
+    sizes = sorted(set(len(m.hx) for m in models))
+    return {"workload": "serving_stream", "requests": len(models), "grids": sizes,
+            "capacity_models_per_s": cap, "arrival_rate_per_s": 1.2 * cap,
+            "models_per_s": lat["models_per_s"], "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
+            "mean_queue_ms": lat["mean_queue_ms"], "failed": sat["failed"] + lat["failed"],
+            "sample_requests": k, "served_mixed_sample_models_per_s": sat_k["models_per_s"],
+            "fp64_one_at_a_time_sample_models_per_s": fp64_rate}
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, as it stands, on the same workload and metric."""
     ws, rank, _ = _dist()
@@ -211,6 +255,7 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="randblock128", choices=sorted(WORKLOADS))
+    ap.add_argument("--serve-requests", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -325,6 +370,8 @@ def main():
     e2e = {"value": e2e_steps / (time.perf_counter() - t0) if e2e_steps else None, "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    serving = run_serving_sample(args.serve_requests, stream) if args.serve_requests > 0 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, secs, desc = cpu_oracle_sample(model, shifts, ORACLE_ITERS_128 if nside == 128 else iters_mixed)
@@ -342,7 +389,7 @@ def main():
                 "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                 "iters_per_shift_mixed": iters_mixed.tolist(), "relres_mixed": relres_mixed.tolist(),
                 "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(n1 - n0), "clocks": clocks}
+                "gpu_launches": int(n1 - n0), "clocks": clocks, "serving": serving}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
