@@ -41,12 +41,12 @@ HBM_FALLBACK_GBS = 6800.0
 # preconditioner (complex FP32 = 8 B; a nodal vector is 1/3 of an edge vector: 8/3 B per edge):
 NODE = 8.0 / 3.0
 PASS_BYTES = {
-    "stencil": 16.0 + 16.0 + 4.0 + 3 * NODE,   # read w, a_old, M_e, psi, b_old; write a, q, b
-    "update": 32.0 + 16.0 + 4.0 + 3 * NODE,    # read x, w, a, q, M_e, x_n, b; write x, w, x_n
-    "nodal": 8.0 + 4.0 + 4 * NODE,             # read x, M_e, x_n, cn, W_n (4 B/node); write psi
+    # read w, a_old, M_e, psi, b_old; write a, q, b, G^T M p
+    "stencil": 16.0 + 16.0 + 4.0 + 4 * NODE,
+    # read x, w, a, q, M_e, diag K; x_n, b, u, G^T M p, cn, W_n; write x, w; x_n, u, psi
+    "update": 32.0 + 16.0 + 8.0 + 8 * NODE + 0.5 * NODE,
 }
-KERNEL_NAMES = {"stencil": "k_cocg_stencil<float>", "update": "k_cocg_update<float>",
-                "nodal": "k_cocg_nodal<float>"}
+KERNEL_NAMES = {"stencil": "k_cocg_stencil<float>", "update": "k_cocg_update<float>"}
 
 
 def _dist():
@@ -352,7 +352,7 @@ def main():
                 "algorithmic_bytes_per_launch": PASS_BYTES[dom] * units, "units_per_launch": units,
                 "iteration_gbs": sum(PASS_BYTES.values()) * units / (it_ms * 1e-3) / 1e9,
                 "iteration_frac": sum(PASS_BYTES.values()) * units / (it_ms * 1e-3) / 1e9 / peak,
-                "pass_ms": {k: prof[k + "_ms"] for k in ("stencil", "update", "nodal", "residual")},
+                "pass_ms": {k: prof[k + "_ms"] for k in ("stencil", "update", "residual")},
                 "pass_gbs": gbs}
 
     # end to end through the C ABI from host buffers: grid upload + forward + result read-back

@@ -293,10 +293,10 @@ int64_t tem_launch_count(void);
  * tem_forward for `s` shifts (same loop source; precision and preconditioner as given), runs one
  * FP64 residual pass and then `n_iter` COCG iterations with CUDA events around
  * every launch on `cuda_stream`, and writes the average duration in ms of
- *   ms_out[0] : the stencil pass  (z = D^-1 r + G psi, p <- z + beta p, q <- A p, (p, q)),
- *   ms_out[1] : the update pass   (x += alpha p, r -= alpha q),
+ *   ms_out[0] : the stencil pass  (a, b <- z parts + beta a, b; q <- A (a + G b); G^T M p; (p, q)),
+ *   ms_out[1] : the update pass   (x, x_n, r, w = D^-1 r, G^T M d, psi; (r, z), ||r||),
  *   ms_out[2] : the FP64 residual pass,
- *   ms_out[3] : the nodal pass    (psi = D_n^-1 G^T r, (r, z), ||r||),
+ *   ms_out[3] : 0 (kept for layout; the nodal work is part of passes 0 and 1),
  * and units_out[0] = interior edges x shifts processed per launch.
  * Slots that converge before n_iter stop being timed; use n_iter small enough.
  */

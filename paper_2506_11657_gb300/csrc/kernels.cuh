@@ -283,6 +283,9 @@ __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView
   __syncthreads();
   C2<T> fxm, fym;  // F_x, F_y of plane k-1 at (i, j)
   own_faces_xy<T>(sm, 0, 1, k0 - 1, k0 > 0 ? G.Rz[k0 - 1] : T(0), i, j, ii, jj, g, fxm, fym);
+  if (i < g.nx && j < g.ny)
+    pol.prev_plane(i + (int64_t)g.nx * (j + (int64_t)g.ny * (k0 - 1)), i, j, k0 - 1, sm.P[0][2][jj][ii],
+                   k0 > 0 ? G.Rz[k0 - 1] : T(0));
   int bk = 1;  // buffer of plane k
 #pragma unroll 1
   for (int k = k0; k < k1; ++k) {
@@ -318,6 +321,8 @@ __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView
       } else {
         pol.edge_invalid(2 * g.ncomp + base);
       }
+      pol.node_end(base, i, j, k, sm.P[bk][0][jj][ii - 1], sm.P[bk][1][jj - 1][ii], sm.P[bk][2][jj][ii],
+                   tg.Rx[ii - 1], tg.Ry[jj - 1], tg.Rx[ii], tg.Ry[jj], rz);
       fxm = fx;
       fym = fy;
     }
@@ -399,19 +404,38 @@ struct CocgStencilPol {
   C2<T> xi;
   const GridView* g;
   C2<T> acc;
-  // prefetched nodal values (own node and its +x, +y, +z neighbours) and masses of the own node
-  C2<T> pb[4], po[4];
-  T me[3];
-  C2<T> gb[3];
+  V* __restrict__ gpo;   // G^T M p per own interior node (NULL with Jacobi only)
+  // prefetched nodal values: own node, +x, +y, +z, -x, -y neighbours, and masses
+  C2<T> pb[6], po[6];
+  T me[3], mxm, mym;
+  C2<T> gb[3], pc[3];
+  C2<T> b0;
+  // the own column one plane below: a_z, b, M_z and 1/Lz there
+  C2<T> az_prev, b_prev;
+  T mz_prev, rz_prev;
   __device__ CocgStencilPol(const GridView& gv) : g(&gv) {}
   __device__ static C2<T> L(const V* p, int64_t i) { const V v = __ldg(p + i); return C2<T>(v.x, v.y); }
   __device__ static void S(V* p, int64_t i, C2<T> a) { V v; v.x = a.re; v.y = a.im; p[i] = v; }
+  __device__ C2<T> bnode(int64_t n) const {
+    const C2<T> v = L(psi, n);
+    return use_beta ? v + cmul(beta, L(bold, n)) : v;
+  }
   __device__ C2<T> load(int c, int i, int j, int k, int64_t idx, bool own) {
     if (!edge_valid(c, i, j, k)) return czero<T>();  // boundary: a stays 0 (buffers start zeroed)
     C2<T> v = L(w, idx);
     if (use_beta) v = v + cmul(beta, L(aold, idx));
     if (own) S(anew, idx, v);
     return v;
+  }
+  // the plane below the chunk: a_z there comes from the shared plane, b and M_z from memory
+  __device__ void prev_plane(int64_t n, int, int, int k, C2<T> az, T rzp) {
+    az_prev = az;
+    rz_prev = rzp;
+    b_prev = czero<T>();
+    mz_prev = T(0);
+    if (!psi || k < 0) return;
+    b_prev = bnode(n);
+    mz_prev = __ldg(Me + 2 * g->ncomp + n);
   }
   // issue the loads the edges of node n will need, before the face phase
   __device__ void prefetch(int64_t n, int i, int j, int k) {
@@ -420,29 +444,56 @@ struct CocgStencilPol {
     me[1] = __ldg(Me + nc + n);
     me[2] = __ldg(Me + 2 * nc + n);
     if (!psi) return;
-    const int64_t nb[4] = {n, n + 1, n + g->nx, n + (int64_t)g->nx * g->ny};
-    const bool in[4] = {true, i + 1 < g->nx, j + 1 < g->ny, k + 1 < g->nz};
+    const bool interior = i > 0 && j > 0 && k > 0;
+    mxm = interior ? __ldg(Me + n - 1) : T(0);
+    mym = interior ? __ldg(Me + nc + n - g->nx) : T(0);
+    const int64_t nb[6] = {n, n + 1, n + g->nx, n + (int64_t)g->nx * g->ny, n - 1, n - g->nx};
+    const bool in[6] = {true, i + 1 < g->nx, j + 1 < g->ny, k + 1 < g->nz, interior, interior};
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 6; ++u) {
       pb[u] = in[u] ? L(psi, nb[u]) : czero<T>();
       po[u] = (in[u] && use_beta) ? L(bold, nb[u]) : czero<T>();
     }
   }
   __device__ void node(int64_t n, int, int, int, T rx, T ry, T rz) {   // once per own node
+    pc[0] = pc[1] = pc[2] = czero<T>();
     if (!psi) return;
     C2<T> b[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) b[u] = use_beta ? pb[u] + cmul(beta, po[u]) : pb[u];
-    S(bnew, n, b[0]);
+    b0 = b[0];
+    S(bnew, n, b0);
     gb[0] = rx * (b[1] - b[0]);
     gb[1] = ry * (b[2] - b[0]);
     gb[2] = rz * (b[3] - b[0]);
   }
   __device__ void edge(int c, int64_t idx, int, int, int, C2<T> a, C2<T> ka) {
     const C2<T> p = psi ? a + gb[c] : a;
+    pc[c] = p;
     const C2<T> qv = ka - cmul(xi, me[c] * p);
     S(q, idx, qv);
     acc = acc + cmul(p, qv);
+  }
+  // (G^T M p)_n from the six edges at node n: +M p / L on the three arriving edges,
+  // -M p / L on the three leaving ones; then roll the column state up one plane
+  __device__ void node_end(int64_t n, int i, int j, int k, C2<T> ax_m, C2<T> ay_m, C2<T> az_own,
+                           T rx_m, T ry_m, T rx, T ry, T rz) {
+    if (psi) {
+      if (i > 0 && j > 0 && k > 0) {
+        const C2<T> bxm = use_beta ? pb[4] + cmul(beta, po[4]) : pb[4];
+        const C2<T> bym = use_beta ? pb[5] + cmul(beta, po[5]) : pb[5];
+        const C2<T> pxm = ax_m + rx_m * (b0 - bxm);
+        const C2<T> pym = ay_m + ry_m * (b0 - bym);
+        const C2<T> pzm = az_prev + rz_prev * (b0 - b_prev);
+        const C2<T> v = (rx_m * mxm) * pxm + (ry_m * mym) * pym + (rz_prev * mz_prev) * pzm -
+                        (rx * me[0]) * pc[0] - (ry * me[1]) * pc[1] - (rz * me[2]) * pc[2];
+        S(gpo, n, v);
+      }
+      b_prev = b0;
+      mz_prev = me[2];
+    }
+    az_prev = az_own;
+    rz_prev = rz;
   }
   __device__ void edge_invalid(int64_t idx) { S(q, idx, czero<T>()); }
 };
@@ -467,6 +518,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_cocg_stencil(Bat
   pol.bold = static_cast<const V*>(S->parity ? d.b1 : d.b0);
   pol.bnew = static_cast<V*>(S->parity ? d.b0 : d.b1);
   pol.q = static_cast<V*>(d.q);
+  pol.gpo = static_cast<V*>(d.gp);
   pol.Me = Geo<T>(d.g).Me;
   pol.beta = C2<T>(T(S->beta_re), T(S->beta_im));
   pol.use_beta = !(S->beta_re == 0.0 && S->beta_im == 0.0);
@@ -492,6 +544,338 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_cocg_stencil(Bat
       S->alpha_im = (S->rho_im * tot[0] - S->rho_re * tot[1]) / den;
     }
   }
+}
+
+// --------------------------- pass A, FP32, asynchronously pipelined through shared memory
+// The same arithmetic as k_cocg_stencil with the raw inputs of each z plane (w, a_old on the
+// edges; psi, b_old on the nodes; tile plus one-node halo) streamed into a three-stage
+// shared ring by cp.async two planes ahead of the compute.  a = w + beta a_old and
+// b = psi + beta b_old are formed in shared memory for planes k and k+1, so every gradient
+// (G b) and every (G^T M p) term reads shared memory.  Out-of-grid halo entries are
+// zero-filled by the copies; boundary entries are stored as zeros.
+namespace pipe {
+constexpr int NA = 8;              // staged arrays: w[3], a_old[3], psi, b_old
+constexpr int NS = 3;              // stages
+constexpr int PLANE = PY * PX;     // entries of one component plane (with halo)
+struct Smem {
+  float2 stage[NS][NA][PLANE];     // raw planes
+  float2 P[2][4][PLANE];           // a (3 components) and b for planes k, k+1
+  float2 F[3][FY][FX];             // faces of plane k
+  TileGeo<float> geo;
+  double red[NT / 32 * 4];
+};
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  const int sz = pred ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void wait_pending() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+}  // namespace pipe
+
+struct PipeArgs {
+  const float2* w; const float2* aold; const float2* psi; const float2* bold;
+  bool use_beta, nodal;
+};
+
+// The halo positions a thread copies and forms are the same on every plane: up to
+// PPT = ceil(PLANE / NT) positions, with their shared index, in-plane offset i + nx j
+// (or -1 outside the grid) and whether they are own (interior of the tile).
+constexpr int PPT = (pipe::PLANE + NT - 1) / NT;
+struct PipePos {
+  int r[PPT];
+  int64_t off[PPT];
+  bool own[PPT];
+};
+
+__device__ __forceinline__ void pipe_positions(PipePos& pp, int i0, int j0, const GridView& g) {
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int r = threadIdx.x + u * NT;
+    pp.r[u] = r < pipe::PLANE ? r : -1;
+    const int jj = r / PX, ii = r - jj * PX;
+    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+    const bool in = r < pipe::PLANE && i >= 0 && i < g.nx && j >= 0 && j < g.ny;
+    pp.off[u] = in ? i + (int64_t)g.nx * j : -1;
+    pp.own[u] = in && ii >= 1 && ii <= TX && jj >= 1 && jj <= TY;
+  }
+}
+
+// issue the copies of plane k into stage st; planes past klast are skipped
+__device__ __forceinline__ void pipe_issue(pipe::Smem& sm, const PipePos& pp, int st, int k, int klast,
+                                           const GridView& g, const PipeArgs& pa) {
+  if (k > klast) return;
+  const bool kin = k >= 0 && k < g.nz;
+  const int64_t gk = (int64_t)g.nx * g.ny * k;
+  const int64_t nc = g.ncomp;
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int r = pp.r[u];
+    if (r < 0) continue;
+    const bool in = kin && pp.off[u] >= 0;
+    const int64_t n = in ? gk + pp.off[u] : 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      pipe::cp_async8(&sm.stage[st][c][r], in ? pa.w + c * nc + n : pa.w, in);
+      const bool ua = in && pa.use_beta;
+      pipe::cp_async8(&sm.stage[st][3 + c][r], ua ? pa.aold + c * nc + n : pa.w, ua);
+    }
+    const bool un = in && pa.nodal;
+    pipe::cp_async8(&sm.stage[st][6][r], un ? pa.psi + n : pa.w, un);
+    const bool ub = un && pa.use_beta;
+    pipe::cp_async8(&sm.stage[st][7][r], ub ? pa.bold + n : pa.w, ub);
+  }
+}
+
+// P[b] <- plane k from stage st; own entries of a and b are written to anew / bnew
+__device__ __forceinline__ void pipe_form(pipe::Smem& sm, const PipePos& pp, int b, int st, int k,
+                                          const GridView& g, C2<float> beta, bool own_plane, float2* anew,
+                                          float2* bnew) {
+  const int64_t gk = (int64_t)g.nx * g.ny * k;
+  const int64_t nc = g.ncomp;
+#pragma unroll
+  for (int u = 0; u < PPT; ++u) {
+    const int r = pp.r[u];
+    if (r < 0) continue;
+    const bool own = own_plane && pp.own[u];
+    const int64_t n = gk + pp.off[u];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float2 v = sm.stage[st][c < 3 ? c : 6][r];
+      const float2 o = sm.stage[st][c < 3 ? 3 + c : 7][r];
+      v.x += beta.re * o.x - beta.im * o.y;
+      v.y += beta.re * o.y + beta.im * o.x;
+      sm.P[b][c][r] = v;
+      if (own) {
+        if (c < 3) anew[c * nc + n] = v;
+        else if (bnew) bnew[n] = v;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void pipe_faces(pipe::Smem& sm, int bk, int bk1, float rLz, float sZ, int i0, int j0,
+                                           const GridView& g) {
+  const float inv_mu0 = float(1.0 / TEM_MU0);
+  const TileGeo<float>& tg = sm.geo;
+  for (int t = threadIdx.x; t < FY * FX; t += NT) {
+    const int jj = t / FX, ii = t - jj * FX;
+    const int i = i0 - 1 + ii, j = j0 - 1 + jj;
+    float2 fx = make_float2(0.f, 0.f), fy = fx, fz = fx;
+    if (i >= 0 && i < g.nx && j >= 0 && j < g.ny) {
+      const int r = jj * PX + ii;
+      const float rLx = tg.Rx[ii], rLy = tg.Ry[jj];
+      const float2 px = sm.P[bk][0][r], py = sm.P[bk][1][r], pz = sm.P[bk][2][r];
+      const float2 pz_j1 = sm.P[bk][2][r + PX], pz_i1 = sm.P[bk][2][r + 1];
+      const float2 px_j1 = sm.P[bk][0][r + PX], py_i1 = sm.P[bk][1][r + 1];
+      const float2 px_k1 = sm.P[bk1][0][r], py_k1 = sm.P[bk1][1][r];
+      const float sx = tg.Sx[ii] * inv_mu0, sy = tg.Sy[jj] * inv_mu0;
+      fx.x = sx * (rLz * (py.x - py_k1.x) + rLy * (pz_j1.x - pz.x));
+      fx.y = sx * (rLz * (py.y - py_k1.y) + rLy * (pz_j1.y - pz.y));
+      fy.x = sy * (rLx * (pz.x - pz_i1.x) + rLz * (px_k1.x - px.x));
+      fy.y = sy * (rLx * (pz.y - pz_i1.y) + rLz * (px_k1.y - px.y));
+      fz.x = sZ * (rLy * (px.x - px_j1.x) + rLx * (py_i1.x - py.x));
+      fz.y = sZ * (rLy * (px.y - px_j1.y) + rLx * (py_i1.y - py.y));
+    }
+    sm.F[0][jj][ii] = fx;
+    sm.F[1][jj][ii] = fy;
+    sm.F[2][jj][ii] = fz;
+  }
+}
+
+static __global__ void __launch_bounds__(NT, 2) k_cocg_stencil_pipe(BatchArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pipe::Smem& sm = *reinterpret_cast<pipe::Smem*>(smem_raw);
+  const int slot = A.blk2slot[blockIdx.x];
+  SlotScalars* S = A.sc + slot;
+  if (!S->active) return;
+  const SlotDesc& d = A.slots[slot];
+  const GridView& g = d.g;
+  const int lb = blockIdx.x - d.blk_stencil0;
+  int i0, j0, k0, k1;
+  tile_of(d, lb, g.nz, i0, j0, k0, k1);
+  PipeArgs pa;
+  pa.w = static_cast<const float2*>(d.w);
+  pa.aold = static_cast<const float2*>(S->parity ? d.a1 : d.a0);
+  pa.psi = static_cast<const float2*>(d.psi);
+  pa.bold = static_cast<const float2*>(S->parity ? d.b1 : d.b0);
+  pa.use_beta = !(S->beta_re == 0.0 && S->beta_im == 0.0);
+  pa.nodal = d.nodal != 0;
+  float2* anew = static_cast<float2*>(S->parity ? d.a0 : d.a1);
+  float2* bnew = pa.nodal ? static_cast<float2*>(S->parity ? d.b0 : d.b1) : nullptr;
+  float2* q = static_cast<float2*>(d.q);
+  float2* gpo = static_cast<float2*>(d.gp);
+  const C2<float> beta(pa.use_beta ? float(S->beta_re) : 0.f, pa.use_beta ? float(S->beta_im) : 0.f);
+  const C2<float> xi(float(d.xi_re), float(d.xi_im));
+  const Geo<float> G(g);
+  const float* __restrict__ Me = G.Me;
+  // stage geometry, start the first three planes
+  stage_geometry<float>(sm.geo, G, g, i0, j0, k0, k1);
+  PipePos pp;
+  pipe_positions(pp, i0, j0, g);
+  // plane p lives in stage (p - k0 + 1) mod NS; planes k0-1 .. k1 are needed
+  pipe_issue(sm, pp, 0, k0 - 1, k1, g, pa);
+  pipe::commit();
+  pipe_issue(sm, pp, 1, k0, k1, g, pa);
+  pipe::commit();
+  pipe_issue(sm, pp, 2, k0 + 1, k1, g, pa);
+  pipe::commit();
+  pipe::wait_pending<1>();
+  __syncthreads();
+  pipe_form(sm, pp, 0, 0, k0 - 1, g, beta, false, anew, bnew);
+  pipe_form(sm, pp, 1, 1, k0, g, beta, true, anew, bnew);
+  __syncthreads();
+  pipe_issue(sm, pp, 0, k0 + 2, k1, g, pa);
+  pipe::commit();
+  const int a_ = threadIdx.x % TX, b_ = threadIdx.x / TX;
+  const int i = i0 + a_, j = j0 + b_;
+  const int ii = a_ + 1, jj = b_ + 1, rr0 = jj * PX + ii;
+  const bool mine = i < g.nx && j < g.ny;
+  const int64_t nc = g.ncomp;
+  const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
+  const float inv_mu0 = float(1.0 / TEM_MU0);
+  // F_x, F_y of plane k0-1 at the own column, and the column state one plane below
+  float2 fxm = make_float2(0.f, 0.f), fym = fxm;
+  float2 az_prev = sm.P[0][2][rr0], b_prev = sm.P[0][3][rr0];
+  float mz_prev = 0.f, rz_prev = 0.f;
+  if (mine && k0 > 0) {
+    const int km = k0 - 1;
+    const float rLz = G.Rz[km];
+    const TileGeo<float>& tg = sm.geo;
+    const float2 px = sm.P[0][0][rr0], py = sm.P[0][1][rr0], pz = sm.P[0][2][rr0];
+    const float sx = tg.Sx[ii] * inv_mu0, syy = tg.Sy[jj] * inv_mu0;
+    const float2 pyk = sm.P[1][1][rr0], pxk = sm.P[1][0][rr0];
+    const float2 pzj = sm.P[0][2][rr0 + PX], pzi = sm.P[0][2][rr0 + 1];
+    fxm.x = sx * (rLz * (py.x - pyk.x) + tg.Ry[jj] * (pzj.x - pz.x));
+    fxm.y = sx * (rLz * (py.y - pyk.y) + tg.Ry[jj] * (pzj.y - pz.y));
+    fym.x = syy * (tg.Rx[ii] * (pz.x - pzi.x) + rLz * (pxk.x - px.x));
+    fym.y = syy * (tg.Rx[ii] * (pz.y - pzi.y) + rLz * (pxk.y - px.y));
+    mz_prev = __ldg(Me + 2 * nc + i + sy * j + sz * km);
+    rz_prev = rLz;
+  }
+  C2<float> acc = czero<float>();
+  int bk = 1;
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k) {
+    const int bk1 = bk ^ 1;
+    const int st_next = (k - k0 + 2) % pipe::NS;      // stage holding plane k+1
+    pipe::wait_pending<1>();                           // plane k+1 has landed (k+2 may be in flight)
+    __syncthreads();
+    pipe_form(sm, pp, bk1, st_next, k + 1, g, beta, k + 1 < k1, anew, bnew);
+    __syncthreads();
+    pipe_issue(sm, pp, (k - k0 + 1) % pipe::NS, k + 3, k1, g, pa);  // into plane k's stage, read last round
+    pipe::commit();
+    const float lz = G.Lz[k], rz = G.Rz[k], szm = G.Sz[k] * inv_mu0;
+    const int64_t n = i + sy * j + sz * k;
+    const bool interior = mine && i > 0 && j > 0 && k > 0;
+    float me0 = 0.f, me1 = 0.f, me2 = 0.f, mxm = 0.f, mym = 0.f;
+    if (mine) {
+      me0 = __ldg(Me + n);
+      me1 = __ldg(Me + nc + n);
+      me2 = __ldg(Me + 2 * nc + n);
+    }
+    if (interior && pa.nodal) {
+      mxm = __ldg(Me + n - 1);
+      mym = __ldg(Me + nc + n - sy);
+    }
+    pipe_faces(sm, bk, bk1, rz, szm, i0, j0, g);
+    __syncthreads();
+    if (mine) {
+      const TileGeo<float>& tg = sm.geo;
+      const float2 fx = sm.F[0][jj][ii], fy = sm.F[1][jj][ii], fz = sm.F[2][jj][ii];
+      const float2 ax = sm.P[bk][0][rr0], ay = sm.P[bk][1][rr0], az = sm.P[bk][2][rr0];
+      const float2 b0 = sm.P[bk][3][rr0];
+      // (G b) on the three leaving edges
+      float2 gx = make_float2(0.f, 0.f), gy = gx, gz = gx;
+      if (pa.nodal) {
+        const float2 bxp = sm.P[bk][3][rr0 + 1], byp = sm.P[bk][3][rr0 + PX], bzp = sm.P[bk1][3][rr0];
+        gx = make_float2(tg.Rx[ii] * (bxp.x - b0.x), tg.Rx[ii] * (bxp.y - b0.y));
+        gy = make_float2(tg.Ry[jj] * (byp.x - b0.x), tg.Ry[jj] * (byp.y - b0.y));
+        gz = make_float2(rz * (bzp.x - b0.x), rz * (bzp.y - b0.y));
+      }
+      float2 pc[3] = {make_float2(ax.x + gx.x, ax.y + gx.y), make_float2(ay.x + gy.x, ay.y + gy.y),
+                      make_float2(az.x + gz.x, az.y + gz.y)};
+      float2 kp[3];
+      {
+        const float2 fzj = sm.F[2][jj - 1][ii], fzi = sm.F[2][jj][ii - 1];
+        const float2 fyi = sm.F[1][jj][ii - 1], fxj = sm.F[0][jj - 1][ii];
+        const float lx = tg.Lx[ii], ly = tg.Ly[jj];
+        kp[0] = make_float2(lx * ((fz.x - fzj.x) - (fy.x - fym.x)), lx * ((fz.y - fzj.y) - (fy.y - fym.y)));
+        kp[1] = make_float2(ly * ((fx.x - fxm.x) - (fz.x - fzi.x)), ly * ((fx.y - fxm.y) - (fz.y - fzi.y)));
+        kp[2] = make_float2(lz * ((fy.x - fyi.x) - (fx.x - fxj.x)), lz * ((fy.y - fyi.y) - (fx.y - fxj.y)));
+      }
+      const float mc[3] = {me0, me1, me2};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float2 qv = make_float2(0.f, 0.f);
+        if (edge_valid(c, i, j, k)) {
+          const float mr = mc[c] * pc[c].x, mi = mc[c] * pc[c].y;
+          qv.x = kp[c].x - (xi.re * mr - xi.im * mi);
+          qv.y = kp[c].y - (xi.re * mi + xi.im * mr);
+          acc.re += pc[c].x * qv.x - pc[c].y * qv.y;
+          acc.im += pc[c].x * qv.y + pc[c].y * qv.x;
+        }
+        q[c * nc + n] = qv;
+      }
+      if (interior && pa.nodal) {
+        // (G^T M p)_n: +M p / L on the arriving edges, -M p / L on the leaving ones
+        const float2 axm = sm.P[bk][0][rr0 - 1], aym = sm.P[bk][1][rr0 - PX];
+        const float2 bxm = sm.P[bk][3][rr0 - 1], bym = sm.P[bk][3][rr0 - PX];
+        const float rxm = tg.Rx[ii - 1], rym = tg.Ry[jj - 1];
+        const float2 pxm = make_float2(axm.x + rxm * (b0.x - bxm.x), axm.y + rxm * (b0.y - bxm.y));
+        const float2 pym = make_float2(aym.x + rym * (b0.x - bym.x), aym.y + rym * (b0.y - bym.y));
+        const float2 pzm = make_float2(az_prev.x + rz_prev * (b0.x - b_prev.x), az_prev.y + rz_prev * (b0.y - b_prev.y));
+        const float cx = rxm * mxm, cy = rym * mym, cz = rz_prev * mz_prev;
+        const float ox = tg.Rx[ii] * me0, oy = tg.Ry[jj] * me1, oz = rz * me2;
+        float2 v;
+        v.x = cx * pxm.x + cy * pym.x + cz * pzm.x - ox * pc[0].x - oy * pc[1].x - oz * pc[2].x;
+        v.y = cx * pxm.y + cy * pym.y + cz * pzm.y - ox * pc[0].y - oy * pc[1].y - oz * pc[2].y;
+        gpo[n] = v;
+      }
+      fxm = fx;
+      fym = fy;
+      az_prev = az;
+      b_prev = b0;
+      mz_prev = me2;
+      rz_prev = rz;
+    }
+    bk = bk1;
+  }
+  pipe::wait_pending<0>();
+  double v[2] = {double(acc.re), double(acc.im)};
+  block_sum<2, NT>(v, sm.red);
+  double* part = A.part + (int64_t)slot * A.part_stride;
+  if (publish_partial<2>(v, part, A.ticket + slot, d.nblk_stencil, lb)) {
+    double tot[2];
+    sum_partials<2, NT>(part, d.nblk_stencil, tot, sm.red);
+    if (threadIdx.x != 0) return;
+    const double den = tot[0] * tot[0] + tot[1] * tot[1];
+    if (!(den > 0.0) || !isfinite(den)) {
+      S->status = TEM_EBREAKDOWN;
+      S->active = 0;
+      S->total_iters += S->iters;
+      atomicSub(A.n_active, 1);
+    } else {
+      S->alpha_re = (S->rho_re * tot[0] + S->rho_im * tot[1]) / den;
+      S->alpha_im = (S->rho_im * tot[0] - S->rho_re * tot[1]) / den;
+    }
+  }
+}
+
+// Launch pass A in FP32 through the pipelined kernel (dynamic shared memory above 48 KB).
+static inline cudaError_t launch_stencil_pipe(const BatchArgs& A, int nblk, cudaStream_t st) {
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(k_cocg_stencil_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)sizeof(pipe::Smem));
+    if (e != cudaSuccess) return e;
+    attr_done[dev] = true;
+  }
+  k_cocg_stencil_pipe<<<nblk, NT, sizeof(pipe::Smem), st>>>(A);
+  return cudaGetLastError();
 }
 
 // Convergence test and the next beta, from rho = (r, z) and rr = ||r||^2 (last CTA only).
@@ -600,12 +984,25 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
       rr += r.re * r.re + r.im * r.im;
     }
   }
-  for (int64_t e = max(e0, ne) + threadIdx.x; e < e1; e += NT) {  // nodal part of the correction
+  // nodal part: x_n += alpha b;  u = G^T M d += alpha G^T M p;  psi = (cn + xi u) / D_n
+  const T* __restrict__ Wn = Geo<T>(g).Wn;
+  C2<T> rn = czero<T>();
+  for (int64_t e = max(e0, ne) + threadIdx.x; e < e1; e += NT) {
     const int64_t m = e - ne;
     C2<T> xn = cmul(alpha, ld<T>(b, m));
     if (!first) xn = xn + ld<T>(d.xn, m);
     st<T>(d.xn, m, xn);
+    const T wn = __ldg(Wn + m);
+    if (wn == T(0)) continue;  // boundary node
+    C2<T> uv = cmul(alpha, ld<T>(d.gp, m));
+    if (!first) uv = uv + ld<T>(d.u, m);
+    st<T>(d.u, m, uv);
+    const C2<T> dv = ld<T>(d.cn, m) + cmul(xi, uv);
+    const C2<T> ps = cdiv(dv, wn * C2<T>(-xi.re, -xi.im));
+    st<T>(d.psi, m, ps);
+    rn = rn + cmul(dv, ps);
   }
+  rz = rz + rn;
   double v[3] = {double(rz.re), double(rz.im), double(rr)};
   block_sum<3, NT>(v, red);
   double* part = A.part + (int64_t)slot * A.part_stride;
@@ -613,13 +1010,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
     double tot[3];
     sum_partials<3, NT>(part, d.nblk_update, tot, red);
     if (threadIdx.x != 0) return;
-    if (d.nodal) {  // the nodal pass adds (G^T r, psi) and decides
-      S->rhoe_re = tot[0];
-      S->rhoe_im = tot[1];
-      S->rr = tot[2];
-    } else {
-      finish_iteration(S, A.n_active, tot[0], tot[1], tot[2]);
-    }
+    finish_iteration(S, A.n_active, tot[0], tot[1], tot[2]);
   }
 }
 
@@ -760,6 +1151,9 @@ struct ResidualPol {
   }
   template <class U> __device__ void node(int64_t, int, int, int, U, U, U) {}
   __device__ void prefetch(int64_t, int, int, int) {}
+  template <class C, class U> __device__ void prev_plane(int64_t, int, int, int, C, U) {}
+  template <class C, class U>
+  __device__ void node_end(int64_t, int, int, int, C, C, C, U, U, U, U, U) {}
   __device__ void edge(int c, int64_t idx, int i, int j, int k, C2<double> xv, C2<double> kx) {
     const C2<double> ax = kx - cmul(xi, Me[idx] * xv);
     const C2<double> b = rhs_c ? ld<double>(rhs_c, idx) : C2<double>(f[idx], 0.0);
@@ -863,6 +1257,8 @@ struct ApplyPol {
   __device__ C2<T> load(int, int, int, int, int64_t idx, bool) { return ld<T>(p, idx); }
   __device__ void node(int64_t, int, int, int, T, T, T) {}
   __device__ void prefetch(int64_t, int, int, int) {}
+  __device__ void prev_plane(int64_t, int, int, int, C2<T>, T) {}
+  __device__ void node_end(int64_t, int, int, int, C2<T>, C2<T>, C2<T>, T, T, T, T, T) {}
   __device__ void edge(int, int64_t idx, int, int, int, C2<T> pv, C2<T> kp) {
     st<T>(q, idx, kp - cmul(xi, Me[idx] * pv));
   }

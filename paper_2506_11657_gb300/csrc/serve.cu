@@ -190,7 +190,7 @@ struct tem_server {
       d.xi_re = r.xi[2 * i];
       d.xi_im = r.xi[2 * i + 1];
       d.x = v.x; d.w = v.w; d.a0 = v.a0; d.a1 = v.a1; d.q = v.q;
-      d.xn = v.xn; d.psi = v.psi; d.b0 = v.b0; d.b1 = v.b1; d.cn = v.cn;
+      d.xn = v.xn; d.psi = v.psi; d.b0 = v.b0; d.b1 = v.b1; d.cn = v.cn; d.u = v.u; d.gp = v.gp;
       d.x64[0] = v.x64[0];
       d.x64[1] = v.x64[1];
       d.f = r.fbuf.as<double>();
@@ -273,13 +273,11 @@ struct tem_server {
     if (opt.solver.precision == TEM_PREC_FP64) {
       k_cocg_stencil<double><<<nblk_s, NT, 0, st>>>(A);
       k_cocg_update<double><<<nblk_u, NT, 0, st>>>(A);
-      if (nodal) k_cocg_nodal<double, false><<<nblk_n, NT, 0, st>>>(A);
     } else {
-      k_cocg_stencil<float><<<nblk_s, NT, 0, st>>>(A);
+      TEM_CUDA_TRY(launch_stencil_pipe(A, nblk_s, st));
       k_cocg_update<float><<<nblk_u, NT, 0, st>>>(A);
-      if (nodal) k_cocg_nodal<float, false><<<nblk_n, NT, 0, st>>>(A);
     }
-    count_launch(nodal ? 3 : 2);
+    count_launch(2);
     TEM_CUDA_TRY(cudaGetLastError());
     return TEM_OK;
   }

@@ -24,12 +24,12 @@ int64_t launch_count() { return g_launches.load(); }
 static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Per slot: x64[2] (FP64 edge vectors), then x, w, a0, a1, q (inner edge vectors) and
-// xn, psi, b0, b1, cn (inner nodal vectors) in the inner precision.
+// xn, psi, b0, b1, cn, u, gp (inner nodal vectors) in the inner precision.
 size_t slot_vector_bytes(int64_t ncomp, int precision) {
   const size_t es = precision == TEM_PREC_FP64 ? 16 : 8;
   const size_t v64 = align256(3 * (size_t)ncomp * 16);
   const size_t ve = align256(3 * (size_t)ncomp * es), vn = align256((size_t)ncomp * es);
-  return 2 * v64 + 5 * ve + 5 * vn;
+  return 2 * v64 + 5 * ve + 7 * vn;
 }
 
 SlotVectors carve_slot(void* base, int64_t ncomp, int precision) {
@@ -44,6 +44,7 @@ SlotVectors carve_slot(void* base, int64_t ncomp, int precision) {
   v.x = e; v.w = e + ve; v.a0 = e + 2 * ve; v.a1 = e + 3 * ve; v.q = e + 4 * ve;
   char* n = e + 5 * ve;
   v.xn = n; v.psi = n + vn; v.b0 = n + 2 * vn; v.b1 = n + 3 * vn; v.cn = n + 4 * vn;
+  v.u = n + 5 * vn; v.gp = n + 6 * vn;
   return v;
 }
 
@@ -83,6 +84,8 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
   d.b0 = v.b0;
   d.b1 = v.b1;
   d.cn = v.cn;
+  d.u = v.u;
+  d.gp = v.gp;
   d.x64[0] = v.x64[0];
   d.x64[1] = v.x64[1];
   d.f = f_real;
@@ -171,12 +174,13 @@ static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& 
 
 int Batch::launch_stencil(cudaStream_t st) {
   BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
-  if (precision_ == TEM_PREC_FP64)
+  if (precision_ == TEM_PREC_FP64) {
     k_cocg_stencil<double><<<nblk_stencil_, NT, 0, st>>>(A);
-  else
-    k_cocg_stencil<float><<<nblk_stencil_, NT, 0, st>>>(A);
+    TEM_CUDA_TRY(cudaGetLastError());
+  } else {
+    TEM_CUDA_TRY(launch_stencil_pipe(A, nblk_stencil_, st));
+  }
   count_launch();
-  TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
 }
 
@@ -193,14 +197,12 @@ int Batch::launch_update(cudaStream_t st) {
 
 int Batch::launch_nodal(cudaStream_t st, int init_only) {
   if (!nodal_) return TEM_OK;
+  if (!init_only) return TEM_EINVAL;  // the per-iteration nodal work is inside passes A and B
   BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
-  if (precision_ == TEM_PREC_FP64) {
-    if (init_only) k_cocg_nodal<double, true><<<nblk_nodal_, NT, 0, st>>>(A);
-    else k_cocg_nodal<double, false><<<nblk_nodal_, NT, 0, st>>>(A);
-  } else {
-    if (init_only) k_cocg_nodal<float, true><<<nblk_nodal_, NT, 0, st>>>(A);
-    else k_cocg_nodal<float, false><<<nblk_nodal_, NT, 0, st>>>(A);
-  }
+  if (precision_ == TEM_PREC_FP64)
+    k_cocg_nodal<double, true><<<nblk_nodal_, NT, 0, st>>>(A);
+  else
+    k_cocg_nodal<float, true><<<nblk_nodal_, NT, 0, st>>>(A);
   count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
@@ -208,11 +210,10 @@ int Batch::launch_nodal(cudaStream_t st, int init_only) {
 
 int Batch::launch_iteration(cudaStream_t st) {
   TEM_TRY(launch_stencil(st));
-  TEM_TRY(launch_update(st));
-  return launch_nodal(st, 0);
+  return launch_update(st);
 }
 
-int Batch::launches_per_iteration() const { return nodal_ ? 3 : 2; }
+int Batch::launches_per_iteration() const { return 2; }
 
 int Batch::launch_residual(cudaStream_t st) {
   BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);

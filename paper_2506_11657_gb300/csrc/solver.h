@@ -9,7 +9,7 @@ namespace tem {
 struct SlotVectors {
   void* x64[2];                                   // FP64 iterate (double-buffered)
   void* x; void* w; void* a0; void* a1; void* q;  // inner edge vectors
-  void* xn; void* psi; void* b0; void* b1; void* cn;  // inner nodal vectors
+  void* xn; void* psi; void* b0; void* b1; void* cn; void* u; void* gp;  // inner nodal vectors
 };
 
 // Per-slot bytes of the vectors for one grid with `ncomp` entries per direction.
