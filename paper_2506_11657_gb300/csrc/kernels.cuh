@@ -553,9 +553,15 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_cocg_stencil(Bat
 // b = psi + beta b_old are formed in shared memory for planes k and k+1, so every gradient
 // (G b) and every (G^T M p) term reads shared memory.  Out-of-grid halo entries are
 // zero-filled by the copies; boundary entries are stored as zeros.
+#ifndef TEM_PIPE_STAGES
+#define TEM_PIPE_STAGES 3          // raw planes in the shared ring (>= 2)
+#endif
+#ifndef TEM_PIPE_MIN_CTAS
+#define TEM_PIPE_MIN_CTAS 2        // occupancy target of the pipelined stencil (CTAs per SM)
+#endif
 namespace pipe {
 constexpr int NA = 8;              // staged arrays: w[3], a_old[3], psi, b_old
-constexpr int NS = 3;              // stages
+constexpr int NS = TEM_PIPE_STAGES;
 constexpr int PLANE = PY * PX;     // entries of one component plane (with halo)
 struct Smem {
   float2 stage[NS][NA][PLANE];     // raw planes
@@ -684,7 +690,7 @@ __device__ __forceinline__ void pipe_faces(pipe::Smem& sm, int bk, int bk1, floa
   }
 }
 
-static __global__ void __launch_bounds__(NT, 2) k_cocg_stencil_pipe(BatchArgs A) {
+static __global__ void __launch_bounds__(NT, TEM_PIPE_MIN_CTAS) k_cocg_stencil_pipe(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pipe::Smem& sm = *reinterpret_cast<pipe::Smem*>(smem_raw);
   const int slot = A.blk2slot[blockIdx.x];
@@ -714,19 +720,20 @@ static __global__ void __launch_bounds__(NT, 2) k_cocg_stencil_pipe(BatchArgs A)
   stage_geometry<float>(sm.geo, G, g, i0, j0, k0, k1);
   PipePos pp;
   pipe_positions(pp, i0, j0, g);
-  // plane p lives in stage (p - k0 + 1) mod NS; planes k0-1 .. k1 are needed
-  pipe_issue(sm, pp, 0, k0 - 1, k1, g, pa);
-  pipe::commit();
-  pipe_issue(sm, pp, 1, k0, k1, g, pa);
-  pipe::commit();
-  pipe_issue(sm, pp, 2, k0 + 1, k1, g, pa);
-  pipe::commit();
-  pipe::wait_pending<1>();
+  // plane p lives in stage (p - k0 + 1) mod NS; planes k0-1 .. k1 are needed.  After the
+  // prologue and after every round, the planes k+1 .. k+NS-1 are in flight (one group each).
+  static_assert(pipe::NS >= 2, "two stages at least");
+#pragma unroll
+  for (int u = 0; u < pipe::NS; ++u) {
+    pipe_issue(sm, pp, u, k0 - 1 + u, k1, g, pa);
+    pipe::commit();
+  }
+  pipe::wait_pending<pipe::NS - 2>();
   __syncthreads();
   pipe_form(sm, pp, 0, 0, k0 - 1, g, beta, false, anew, bnew);
-  pipe_form(sm, pp, 1, 1, k0, g, beta, true, anew, bnew);
+  pipe_form(sm, pp, 1, 1 % pipe::NS, k0, g, beta, true, anew, bnew);
   __syncthreads();
-  pipe_issue(sm, pp, 0, k0 + 2, k1, g, pa);
+  pipe_issue(sm, pp, 0, k0 - 1 + pipe::NS, k1, g, pa);
   pipe::commit();
   const int a_ = threadIdx.x % TX, b_ = threadIdx.x / TX;
   const int i = i0 + a_, j = j0 + b_;
@@ -760,11 +767,12 @@ static __global__ void __launch_bounds__(NT, 2) k_cocg_stencil_pipe(BatchArgs A)
   for (int k = k0; k < k1; ++k) {
     const int bk1 = bk ^ 1;
     const int st_next = (k - k0 + 2) % pipe::NS;      // stage holding plane k+1
-    pipe::wait_pending<1>();                           // plane k+1 has landed (k+2 may be in flight)
+    pipe::wait_pending<pipe::NS - 2>();                // plane k+1 has landed
     __syncthreads();
     pipe_form(sm, pp, bk1, st_next, k + 1, g, beta, k + 1 < k1, anew, bnew);
     __syncthreads();
-    pipe_issue(sm, pp, (k - k0 + 1) % pipe::NS, k + 3, k1, g, pa);  // into plane k's stage, read last round
+    // plane k + NS goes into plane k's stage, formed last round
+    pipe_issue(sm, pp, (k - k0 + 1) % pipe::NS, k + pipe::NS, k1, g, pa);
     pipe::commit();
     const float lz = G.Lz[k], rz = G.Rz[k], szm = G.Sz[k] * inv_mu0;
     const int64_t n = i + sy * j + sz * k;
