@@ -46,7 +46,7 @@ PASS_BYTES = {
     # read x, w, a, q, M_e, diag K; x_n, b, u, G^T M p, cn, W_n; write x, w; x_n, u, psi
     "update": 32.0 + 16.0 + 8.0 + 8 * NODE + 0.5 * NODE,
 }
-KERNEL_NAMES = {"stencil": "k_cocg_stencil<float>", "update": "k_cocg_update<float>"}
+KERNEL_NAMES = {"stencil": "k_cocg_stencil_pipe", "update": "k_cocg_update<float>"}
 
 
 def _dist():

@@ -78,6 +78,11 @@ typedef struct tem_options {
   int32_t check_every;   /* iterations between host-side convergence polls (default 32) */
   int32_t keep_state;    /* nonzero: keep the solutions for tem_adjoint (state_out must be non-NULL) */
   int32_t precond;       /* TEM_PRECOND_AUTO (default), TEM_PRECOND_JACOBI or TEM_PRECOND_NODAL */
+  int32_t carry_direction; /* MIXED: 0 (default): every inner solve restarts from the true
+                            residual (plain defect correction); nonzero: an FP64 outer step
+                            replaces the inner residual by the true one and the inner COCG
+                            keeps its search direction (residual replacement).  A solve that
+                            follows a stagnated inner solve restarts either way */
 } tem_options;
 
 /* Preconditioner of the inner COCG sweeps. */
@@ -296,7 +301,8 @@ int64_t tem_launch_count(void);
  *   ms_out[0] : the stencil pass  (a, b <- z parts + beta a, b; q <- A (a + G b); G^T M p; (p, q)),
  *   ms_out[1] : the update pass   (x, x_n, r, w = D^-1 r, G^T M d, psi; (r, z), ||r||),
  *   ms_out[2] : the FP64 residual pass,
- *   ms_out[3] : 0 (kept for layout; the nodal work is part of passes 0 and 1),
+ *   ms_out[3] : not a time: the CTAs per SM the FP32 stencil kernel keeps resident
+ *               (0 for FP64),
  * and units_out[0] = interior edges x shifts processed per launch.
  * Slots that converge before n_iter stop being timed; use n_iter small enough.
  */

@@ -354,7 +354,7 @@ int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_ve
   TEM_CUDA_TRY(cudaEventElapsedTime(&ms, ev[0], ev[1]));
   ms_out[2] = ms;
   TEM_TRY(b.launch_nodal(st, 1));
-  double tot_s = 0, tot_u = 0, tot_n = 0;
+  double tot_s = 0, tot_u = 0;
   for (int it = 0; it < n_iter; ++it) {
     TEM_CUDA_TRY(cudaEventRecord(ev[0], st));
     TEM_TRY(b.launch_stencil(st));
@@ -371,7 +371,7 @@ int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_ve
   }
   ms_out[0] = tot_s / n_iter;
   ms_out[1] = tot_u / n_iter;
-  ms_out[3] = tot_n;  // the nodal work now runs inside the stencil and update passes
+  ms_out[3] = precision == TEM_PREC_MIXED ? stencil_pipe_occupancy() : 0;
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (units_out) {

@@ -234,6 +234,7 @@ void tem_default_options(tem_options* opt) {
   opt->max_outer = 40;
   opt->check_every = 32;
   opt->keep_state = 0;
+  opt->carry_direction = 0;
 }
 
 int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, const double* hz, int64_t nz,

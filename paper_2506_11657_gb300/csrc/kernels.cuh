@@ -886,6 +886,17 @@ static inline cudaError_t launch_stencil_pipe(const BatchArgs& A, int nblk, cuda
   return cudaGetLastError();
 }
 
+// Resident CTAs per SM of the pipelined stencil (0 on error).
+static inline int stencil_pipe_occupancy() {
+  int n = 0;
+  if (cudaFuncSetAttribute(k_cocg_stencil_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(pipe::Smem)) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cocg_stencil_pipe, NT, sizeof(pipe::Smem)) != cudaSuccess)
+    return 0;
+  return n;
+}
+
 // Convergence test and the next beta, from rho = (r, z) and rr = ||r||^2 (last CTA only).
 __device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, double rho_re, double rho_im,
                                                  double rr) {
@@ -902,6 +913,7 @@ __device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, 
     done = true;
   } else if (rr >= S->rr_best && S->iters - S->it_best > S->stall_window) {
     done = true;  // stagnation: end this inner solve; the FP64 outer step restarts from the true residual
+    S->stalled = 1;
   } else {
     if (rr < S->rr_best) {
       S->rr_best = rr;
@@ -924,6 +936,26 @@ __device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, 
     S->total_iters += S->iters;
     atomicSub(n_active, 1);
   }
+}
+
+// The first beta of an inner solve whose right-hand side is s r (r the true FP64 residual).
+// A restart takes beta = 0 (p = z).  A solve that continues the last direction p_prev of the
+// previous inner solve (scale s_prev; its last rho, rho_prev, still in S->rho) takes the COCG
+// beta of the unscaled quantities, rho / rho_prev, times s / s_prev for the scale of the new
+// directions:  beta = (rho_s / rho_prev_s) (s_prev / s),  rho_s = s^2 rho.
+__device__ __forceinline__ void start_direction(SlotScalars* S, double rho_re, double rho_im) {
+  const double den = S->rho_re * S->rho_re + S->rho_im * S->rho_im;
+  if (S->carry_ratio > 0.0 && den > 0.0 && isfinite(den)) {
+    const double br = (rho_re * S->rho_re + rho_im * S->rho_im) / den;
+    const double bi = (rho_im * S->rho_re - rho_re * S->rho_im) / den;
+    S->beta_re = br / S->carry_ratio;
+    S->beta_im = bi / S->carry_ratio;
+  } else {
+    S->beta_re = 0.0;
+    S->beta_im = 0.0;
+  }
+  S->rho_re = rho_re;
+  S->rho_im = rho_im;
 }
 
 // ---------- pass B: x += alpha a, x_n += alpha b, r = D w - alpha q, w = r / D; (r, D^-1 r), ||r||
@@ -1115,12 +1147,9 @@ __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
     sum_partials<2, NT>(part, d.nblk_nodal, tot, red);
     if (threadIdx.x != 0) return;
     const double rre = S->rhoe_re + tot[0], rim = S->rhoe_im + tot[1];
-    if (pend) {  // first nodal pass of an inner solve: rho_0, beta = 0
+    if (pend) {  // first nodal pass of an inner solve: rho_0 and the first beta
       S->pending = 0;
-      S->rho_re = rre;
-      S->rho_im = rim;
-      S->beta_re = 0.0;
-      S->beta_im = 0.0;
+      start_direction(S, rre, rim);
       S->active = 1;
       return;
     }
@@ -1238,20 +1267,27 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
     const double rel2 = d.fp64_inner ? want : fmax(S->inner_rel2, want);
     S->tol2 = rel2 * S->bb;
     S->iters = 0;
-    S->parity = 0;
     S->rr_best = S->bb;
     S->it_best = 0;
+    // continue the last inner solve's direction (residual replacement), or restart: first
+    // outer step, carrying off, or the last inner solve stagnated
+    const bool carry = S->carry && pol.upd && !S->stalled;
+    S->stalled = 0;
+    if (carry) {
+      S->carry_ratio = sc * S->inv_scale_prev;  // s / s_prev (> 0)
+      S->parity ^= 1;                           // the last direction becomes a_old, b_old
+    } else {
+      S->carry_ratio = 0.0;
+      S->parity = 0;
+    }
     S->inv_scale_prev = 1.0 / sc;
     S->scale = 1.0 / sqrt(tot[0]);
     S->rhoe_re = tot[1];
     S->rhoe_im = tot[2];
-    S->beta_re = 0.0;
-    S->beta_im = 0.0;
     if (d.nodal) {
       S->pending = 1;            // the nodal pass adds (G^T r, psi) to rho_0 and starts the solve
     } else {
-      S->rho_re = tot[1];
-      S->rho_im = tot[2];
+      start_direction(S, tot[1], tot[2]);
       S->active = 1;
     }
     atomicAdd(A.n_active, 1);

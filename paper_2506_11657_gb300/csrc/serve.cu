@@ -211,6 +211,9 @@ struct tem_server {
       S.inv_scale_prev = 1.0;
       S.max_outer = opt.solver.max_outer;
       S.stall_window = 400;
+      S.carry = opt.solver.carry_direction != 0;
+      S.stalled = 0;
+      S.carry_ratio = 0.0;
       slots_h[q] = d;
       sc_h[q] = S;
       owner[q] = (int)r.ticket;

@@ -53,7 +53,7 @@ void decompose_slot(SlotDesc& d, int nodal) {
   d.tiles_y = (d.g.ny + TY - 1) / TY;
   // the longest z chunk (64/32/16/8 planes) that gives the slot alone 2 CTAs per SM (152 SMs)
   const int64_t cols = (int64_t)d.tiles_x * d.tiles_y;
-  d.zchunk = 64;
+  d.zchunk = ZMAX;
   while (d.zchunk > 8 && cols * ((d.g.nz + d.zchunk - 1) / d.zchunk) < 2 * 152) d.zchunk /= 2;
   d.zchunks = (d.g.nz + d.zchunk - 1) / d.zchunk;
   d.nblk_stencil = d.tiles_x * d.tiles_y * d.zchunks;
@@ -136,6 +136,9 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
     S.inv_scale_prev = 1.0;
     S.max_outer = opt.max_outer;
     S.stall_window = 400;
+    S.carry = opt.carry_direction != 0;
+    S.stalled = 0;
+    S.carry_ratio = 0.0;
   }
   TEM_TRY(slots_d_.alloc(ns * sizeof(SlotDesc), st));
   TEM_TRY(sc_d_.alloc(ns * sizeof(SlotScalars), st));

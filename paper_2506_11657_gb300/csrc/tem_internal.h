@@ -185,6 +185,9 @@ struct SlotScalars {
   double rr_best;           // smallest recursive ||r||^2 of the current inner solve
   int32_t it_best;          // iteration that reached it
   int32_t stall_window;     // end the inner solve after this many iterations without a new best
+  int32_t carry;            // keep the search direction across outer steps (residual replacement)
+  int32_t stalled;          // the last inner solve ended on stagnation
+  double carry_ratio;       // s_prev / s of an armed solve that continues the direction, else 0
 };
 
 }  // namespace tem

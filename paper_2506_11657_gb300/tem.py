@@ -37,7 +37,7 @@ class TEMError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("max_iter", C.c_int32), ("tol", C.c_double),
                 ("inner_tol", C.c_double), ("max_outer", C.c_int32), ("check_every", C.c_int32),
-                ("keep_state", C.c_int32), ("precond", C.c_int32)]
+                ("keep_state", C.c_int32), ("precond", C.c_int32), ("carry_direction", C.c_int32)]
 
 
 class ServerOptions(C.Structure):
@@ -286,8 +286,9 @@ def launch_count() -> int:
 
 def profile_passes(grid: Grid, loop_xy, z_loop, shifts, precision=PREC_MIXED, n_iter=20, current=1.0, stream=None,
                    precond=PRECOND_AUTO):
-    """Average CUDA-event time (ms) of the stencil, update and FP64 residual passes, and the
-    interior edges x shifts one launch processes (tem_profile_passes)."""
+    """Average CUDA-event time (ms) of the stencil, update and FP64 residual passes, the CTAs
+    per SM the FP32 stencil keeps resident, and the interior edges x shifts one launch
+    processes (tem_profile_passes)."""
     loop = _f64(loop_xy).reshape(-1, 2)
     shifts = np.ascontiguousarray(shifts, dtype=np.complex128)
     xi = shifts.view(np.float64)
@@ -297,7 +298,8 @@ def profile_passes(grid: Grid, loop_xy, z_loop, shifts, precision=PREC_MIXED, n_
                                     len(shifts), int(precision), int(precond), int(n_iter), _stream(stream), _ptr(ms),
                                     _ptr(units)),
            "tem_profile_passes")
-    return {"stencil_ms": ms[0], "update_ms": ms[1], "residual_ms": ms[2], "nodal_ms": ms[3], "units": units[0]}
+    return {"stencil_ms": ms[0], "update_ms": ms[1], "residual_ms": ms[2],
+            "stencil_ctas_per_sm": int(ms[3]), "units": units[0]}
 
 
 class Server:

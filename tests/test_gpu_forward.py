@@ -57,12 +57,16 @@ def test_tiny16_fp64_matches_oracle(tiny):
     _check(res.d, d_ref, S, 1e-6, 1e-10)
 
 
+@pytest.mark.parametrize("carry", [0, 1])
 @pytest.mark.parametrize("precond", ["nodal", "jacobi"])
-def test_tiny16_mixed_matches_oracle(tiny, precond):
+def test_tiny16_mixed_matches_oracle(tiny, precond, carry):
+    """Both outer schemes: restart every inner solve (carry 0) and residual replacement with
+    the search direction kept across outer steps (carry 1)."""
     from paper_2506_11657_gb300 import tem
     m, shifts, c, rx, d_ref, S = tiny
     grid = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma)
-    opt = tem.default_options(precision="mixed", tol=1e-12, precond=precond, inner_tol=1e-3 if precond == "nodal" else 1e-1)
+    opt = tem.default_options(precision="mixed", tol=1e-12, precond=precond, inner_tol=1e-3 if precond == "nodal" else 1e-1,
+                              carry_direction=carry)
     res = tem.forward(grid, m.loop_xy, m.z_loop, rx, shifts, c, opt)
     assert res.status == tem.TEM_OK
     _check(res.d, d_ref, S, 1e-5, 1e-9)

@@ -91,3 +91,15 @@ def test_build_grid_validates_before_touching_the_device(lib):
 def test_status_strings(lib):
     assert lib.status_string(lib.TEM_OK) == "TEM_OK"
     assert "max_iter" in lib.status_string(lib.TEM_ENOCONV)
+
+
+def test_default_options_and_struct_layout(lib):
+    """tem_default_options fills every field of the binding's struct (the C struct ends with
+    carry_direction; a field added on one side only would shift it)."""
+    import ctypes as C
+    o = lib.Options()
+    C.memset(C.byref(o), 0x7f, C.sizeof(o))
+    lib.lib().tem_default_options(C.byref(o))
+    assert (o.precision, o.max_iter, o.tol, o.inner_tol) == (lib.PREC_FP64, 20000, 1e-12, 1e-3)
+    assert (o.max_outer, o.check_every, o.keep_state, o.precond, o.carry_direction) == (40, 32, 0, 0, 0)
+    assert C.sizeof(o) == 48
