@@ -192,6 +192,16 @@ int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
 int tem_state_stats(const tem_state* state, int32_t* iters, double* relres);
 
 /*
+ * Copy the FP64 solution x_i = (K - xi_i M)^{-1} f of shift i (the solves of Eq. (rmj)) kept in
+ * `state` to host memory.  x_out (caller-owned) holds 2 * 3 * nx * ny * nz doubles, (re, im)
+ * interleaved, in the edge layout of the library: entry (c, i, j, k) at
+ * c * nx*ny*nz + i + nx * (j + ny * k) is the edge of direction c leaving node (i, j, k);
+ * boundary and padding entries are 0.  Synchronises `cuda_stream`.
+ * TEM_EINVAL for a NULL pointer or i outside [0, s).
+ */
+int tem_state_solution(const tem_state* state, int64_t i, void* cuda_stream, double* x_out);
+
+/*
  * Adjoint gradient (Sec. 4): given g = dphi/dd (host, n_rx*K doubles laid
  * out like dbzdt_out), writes grad[c] = dphi/dlog sigma_c for every cell
  * (host, nx*ny*nz doubles):

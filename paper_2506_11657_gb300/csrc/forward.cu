@@ -193,6 +193,17 @@ int tem_state_stats(const tem_state* state, int32_t* iters, double* relres) {
   return TEM_OK;
 }
 
+int tem_state_solution(const tem_state* state, int64_t i, void* cuda_stream, double* x_out) {
+  if (!state || !x_out || !state->batch || i < 0 || i >= state->s) return TEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const SlotDesc& d = state->batch->slots_host()[i];
+  const SlotScalars& S = state->batch->scalars()[i];
+  const size_t bytes = (size_t)3 * state->grid->v.ncomp * 16;
+  TEM_CUDA_TRY(cudaMemcpyAsync(x_out, d.x64[S.xcur], bytes, cudaMemcpyDeviceToHost, st));
+  TEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return TEM_OK;
+}
+
 int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) {
   if (!S || !g || !grad || !S->batch) return TEM_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

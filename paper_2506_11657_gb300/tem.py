@@ -22,7 +22,7 @@ PRECOND_AUTO, PRECOND_JACOBI, PRECOND_NODAL = 0, 1, 2
 
 EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
-            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_adjoint",
+            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_state_solution", "tem_adjoint",
             "tem_state_destroy", "tem_apply_operator", "tem_apply_operator_noalloc", "tem_launch_count",
             "tem_profile_passes", "tem_server_default_options", "tem_server_create", "tem_server_submit",
             "tem_server_step", "tem_server_poll", "tem_server_counts", "tem_server_destroy"]
@@ -80,6 +80,7 @@ def lib():
     L.tem_forward.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, _dp, _dp,
                               C.c_int64, C.c_int64, C.POINTER(Options), C.c_void_p, _dp, C.POINTER(C.c_void_p)]
     L.tem_state_stats.argtypes = [C.c_void_p, _i32p, _dp]
+    L.tem_state_solution.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, _dp]
     L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
     L.tem_state_destroy.argtypes = [C.c_void_p]
     L.tem_apply_operator.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
@@ -212,6 +213,13 @@ class State:
         rr = np.zeros(self.s)
         _check(lib().tem_state_stats(self.handle, it.ctypes.data_as(_i32p), _ptr(rr)), "tem_state_stats")
         return it, rr
+
+    def solution(self, i, stream=None):
+        """FP64 solution x_i of shift i, complex, in the library's edge layout (tem_state_solution)."""
+        out = np.zeros(3 * self.n_cells, dtype=np.complex128)
+        _check(lib().tem_state_solution(self.handle, int(i), _stream(stream), out.view(np.float64).ctypes.data_as(_dp)),
+               "tem_state_solution")
+        return out
 
     def adjoint(self, dphi_dd, stream=None):
         g = _f64(dphi_dd).reshape(self.n_rx, self.K)

@@ -1,0 +1,69 @@
+"""Full-size parity on the 128^3 random-block model (10 shifts, 31 channels), run the way the
+benchmark runs it (mixed precision, default options).  The oracle cannot factor a model of this
+size, so the checks use what holds at any size:
+
+* every FP64 solution x_i the path returns solves the oracle's independently assembled system,
+  ||f - (K - xi_i M) x_i|| <= 1e-11 ||f||  (the path stops at 1e-12 by its own FP64 residual),
+  and is zero on the boundary and padding entries of the layout;
+* the response is the oracle's combination of those solutions (Eq. (rmj), (rmjQ)):
+  d[r, k] = sum_i Re(c[i, k] q_r^T x_i) with the oracle's receiver rows, to 1e-12 S_k,
+  S_k = sum_i |c[i, k] q_r^T x_i|;
+* the mixed-precision response agrees with the all-FP64 path on the same model per channel
+  within 1e-5 |d| + 1e-9 S_k (the mixed bound of the small-model parity tests).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.tem import TEMProblem
+from paper_2506_11657_gb300 import workloads as W
+from tests._layout import lib_index_of_interior
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def run():
+    from paper_2506_11657_gb300 import tem
+    m = W.randblock128()
+    shifts, c, err = tem.poles_residues(m.t, m.degree)
+    grid = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma)
+    res = tem.forward(grid, m.loop_xy, m.z_loop, m.rx, shifts, c, tem.default_options(precision="mixed"),
+                      keep_state=True)
+    assert res.status == tem.TEM_OK
+    xs = [res.state.solution(i) for i in range(len(shifts))]
+    res.state.close()
+    d64 = tem.forward(grid, m.loop_xy, m.z_loop, m.rx, shifts, c, tem.default_options(precision="fp64")).d
+    grid.close()
+    P = TEMProblem(m.hx, m.hy, m.hz, m.sigma, m.loop_xy, m.z_loop, m.rx, origin=m.origin)
+    idx = lib_index_of_interior(P.grid)
+    return m, shifts, c, res.d, d64, xs, P, idx
+
+
+def test_solutions_solve_the_oracle_system(run):
+    m, shifts, c, d, d64, xs, P, idx = run
+    pad = np.ones(xs[0].size, dtype=bool)
+    pad[idx] = False
+    nf = np.linalg.norm(P.f)
+    for i, x in enumerate(xs):
+        assert not np.any(x[pad]), i
+        xi = x[idx]
+        r = P.f - (P.K @ xi - shifts[i] * (P.Md * xi))
+        rel = np.linalg.norm(r) / nf
+        assert rel <= 1e-11, (i, shifts[i], rel)
+
+
+def test_response_is_the_oracle_combination(run):
+    m, shifts, c, d, d64, xs, P, idx = run
+    y = np.stack([P.Q @ x[idx] for x in xs])                      # (s, n_rx)
+    d_ref = np.einsum("ik,ir->rk", c, y).real
+    S = np.einsum("ik,ir->rk", np.abs(c), np.abs(y))
+    assert np.all(np.abs(d - d_ref) <= 1e-12 * S + 1e-300)
+
+
+def test_mixed_agrees_with_fp64_path(run):
+    m, shifts, c, d, d64, xs, P, idx = run
+    y = np.stack([P.Q @ x[idx] for x in xs])
+    S = np.einsum("ik,ir->rk", np.abs(c), np.abs(y))
+    assert np.all(np.abs(d - d64) <= 1e-5 * np.abs(d64) + 1e-9 * S)
