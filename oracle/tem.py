@@ -91,6 +91,24 @@ class TEMProblem:
             g += (s * (D.T @ (lam * xs[i]))).real
         return g
 
+    def jvp(self, shifts, c, dlogsigma, xs=None, method="lu"):
+        """J dm for dm = d log sigma (one value per cell), Sec. 4: with A_i = K - xi_i M(m) and
+        dA_i/dm_c = -xi_i e^{m_c} M_c,  d(A_i^{-1} f)/dm . dm = xi_i A_i^{-1} (sum_c dm_c e^{m_c} M_c) g_i,
+        g_i = A_i^{-1} f, so  (J dm)[r, k] = sum_i Re(c[i, k] xi_i q_r^T A_i^{-1} (dM g_i)),
+        dM = diag(D dm) with D[e, c] = sigma_c V_c / 4 on the cell's edges."""
+        if xs is None:
+            xs = [self.solve(s, method) for s in shifts]
+        dM = self.mass_derivative() @ np.asarray(dlogsigma, dtype=np.float64).ravel()
+        y = []
+        for i, s in enumerate(shifts):
+            b = s * (dM * xs[i])
+            if method == "lu":
+                dx = solve_lu(self.K, self.Md, b, s)
+            else:
+                dx, _, _ = solve_cocg(self.K, self.Md, b, s)
+            y.append(self.Q @ dx)
+        return np.einsum("ik,ir->rk", np.asarray(c), np.stack(y)).real
+
     def dense(self):
         """T0 route for tiny grids."""
         return DenseEig(self.K, self.Md)

@@ -71,3 +71,43 @@ def test_adjoint_matches_finite_differences():
         dm = TEMProblem(m.hx, m.hy, m.hz, sm_, m.loop_xy, m.z_loop, rx, origin=m.origin).forward(sh, c)
         fd = ((dp - dm) * gres).sum() / (2 * delta)
         assert abs(fd - g[cidx]) <= 1e-5 * np.abs(g).max() + 1e-6 * abs(fd), (cidx, fd, g[cidx])
+
+
+def _jvp_model():
+    m = W.uniform_model(6, 20.0, 2, 0.02, 40.0, 1e-5, 1e-3, 7, 8)
+    rng = np.random.default_rng(12)
+    sigma = m.sigma * np.where(m.sigma > 1e-6, 10 ** rng.uniform(-0.5, 0.5, m.sigma.shape), 1.0)
+    rx = np.array([[0.0, 0.0, 0.0], [10.0, -5.0, 0.0], [-20.0, 15.0, 0.0]])
+    sh, c, _ = R.tem_poles_residues(m.t, m.degree)
+    return m, sigma, rx, sh, c, rng
+
+
+def test_jvp_matches_directional_finite_differences():
+    """J dm (Sec. 4) against central differences of the forward along a random direction in
+    log sigma: (d(m + h dm) - d(m - h dm)) / 2h, h = 1e-4 (truncation O(h^2))."""
+    m, sigma, rx, sh, c, rng = _jvp_model()
+    P = TEMProblem(m.hx, m.hy, m.hz, sigma, m.loop_xy, m.z_loop, rx, origin=m.origin)
+    dm = rng.standard_normal(sigma.size)
+    jd = P.jvp(sh, c, dm)
+    h = 1e-4
+    dp = TEMProblem(m.hx, m.hy, m.hz, sigma.ravel() * np.exp(h * dm), m.loop_xy, m.z_loop, rx,
+                    origin=m.origin).forward(sh, c)
+    dn = TEMProblem(m.hx, m.hy, m.hz, sigma.ravel() * np.exp(-h * dm), m.loop_xy, m.z_loop, rx,
+                    origin=m.origin).forward(sh, c)
+    fd = (dp - dn) / (2 * h)
+    assert np.abs(fd - jd).max() <= 1e-6 * np.abs(jd).max()
+    # a direction confined to the air cells moves the response much less than one in the earth
+    air = (sigma.ravel() < 1e-6).astype(float)
+    assert np.abs(P.jvp(sh, c, air)).max() < 1e-3 * np.abs(P.jvp(sh, c, 1.0 - air)).max()
+
+
+def test_jvp_is_the_transpose_of_the_adjoint():
+    """<g, J dm> = <J^T g, dm> with the separately pinned adjoint gradient."""
+    m, sigma, rx, sh, c, rng = _jvp_model()
+    P = TEMProblem(m.hx, m.hy, m.hz, sigma, m.loop_xy, m.z_loop, rx, origin=m.origin)
+    d, xs = P.forward(sh, c, return_solutions=True)
+    dm = rng.standard_normal(sigma.size)
+    g = rng.standard_normal(d.shape)
+    lhs = np.sum(g * P.jvp(sh, c, dm, xs=xs))
+    rhs = np.dot(P.adjoint_gradient(sh, c, g, xs=xs), dm)
+    assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + abs(rhs))
