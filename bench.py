@@ -256,6 +256,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="randblock128", choices=sorted(WORKLOADS))
     ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--no-derivatives", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -340,6 +341,27 @@ def main():
                 "median_rel_err_mixed_vs_fp64": float(np.median(rel)),
                 "channels_rel_le_1e-5": int((rel <= 1e-5).sum()), "channels": int(rel.size)}
 
+    # the derivative actions of Sec. 4 on the same model: J dm (tem_jvp) and J^T g (tem_adjoint),
+    # one batched solve each, timed with CUDA events after a forward that keeps its solutions
+    derivs = None
+    if not args.no_derivatives:
+        rk = fwd(opt_mixed, keep=True)
+        rng = np.random.default_rng(7)
+        dm = rng.standard_normal(model.sigma.size) * (model.sigma.ravel() > 1e-6)
+        g = rng.standard_normal(rk.d.shape)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        jd = rk.state.jvp(dm, stream=stream)
+        e1.record(stream)
+        gr = rk.state.adjoint(g, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        rk.state.close()
+        lhs, rhs = float(np.sum(g * jd)), float(np.dot(gr, dm))
+        derivs = {"jvp_ms": e0.elapsed_time(e1), "adjoint_ms": e1.elapsed_time(e2),
+                  "forward_ms": float(np.median(step_ms)),
+                  "transpose_rel_gap": abs(lhs - rhs) / (np.sum(np.abs(g * jd)) + np.sum(np.abs(gr * dm)))}
+
     # per-kernel timing of the passes (dominant kernel roofline)
     prof = tem.profile_passes(grid, model.loop_xy, model.z_loop, shifts, tem.PREC_MIXED, n_iter=20, stream=stream)
     peak, peak_kind = _peaks()
@@ -389,7 +411,8 @@ def main():
                 "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                 "iters_per_shift_mixed": iters_mixed.tolist(), "relres_mixed": relres_mixed.tolist(),
                 "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": int(n1 - n0), "clocks": clocks, "serving": serving}
+                "gpu_launches": int(n1 - n0), "clocks": clocks, "serving": serving,
+                "derivatives": derivs}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -213,6 +213,21 @@ int tem_state_solution(const tem_state* state, int64_t i, void* cuda_stream, dou
  */
 int tem_adjoint(tem_state* state, const double* dphi_dd, void* cuda_stream, double* grad_logsigma_out);
 
+/*
+ * Linearised forward, the Jacobian-vector product of Sec. 4: for a direction dm in
+ * log sigma (host, nx*ny*nz doubles, one per cell) writes dd = J dm (host, n_rx*K doubles laid
+ * out like dbzdt_out):
+ *   dM_e = sum_{cells c around e} sigma_c dm_c V_c / 4,     b_i = xi_i dM x_i,
+ *   dx_i = (K - xi_i M)^{-1} b_i,                          dd[r, k] = sum_i Re(c[i, k] q_r^T dx_i),
+ * with x_i the forward solutions kept in `state` (one batched solve of the s shifts, the
+ * precision and tolerances of the forward call; the nodal preconditioner adds the
+ * divergence of b_i, which is not zero here).  J^T is tem_adjoint: the two satisfy
+ * <g, J dm> = <tem_adjoint(g), dm>.  A zero direction returns zeros without a solve.
+ * Returns TEM_EINVAL for NULL pointers or a non-finite entry of dm, TEM_ENOCONV (output
+ * written) if a solve hit max_iter.
+ */
+int tem_jvp(tem_state* state, const double* dlogsigma, void* cuda_stream, double* ddbzdt_out);
+
 int tem_state_destroy(tem_state* state);
 
 /*

@@ -63,7 +63,7 @@ int validate_options(const tem_options& o) {
 // Solve (K - xi_i M) x_i = b_i for all shifts of one grid; returns the batch.
 int solve_shifts(const tem_grid* g, const double* xi, int s, const tem_options& opt, cudaStream_t st,
                  const double* f_dev, const void* rhs_c_dev, const double* bnorm2, DevBuf& vec,
-                 std::unique_ptr<Batch>& batch, SolveStats* stats) {
+                 std::unique_ptr<Batch>& batch, SolveStats* stats, int rhs_div = 0) {
   const int64_t ncomp = g->v.ncomp;
   const size_t per = slot_vector_bytes(ncomp, opt.precision);
   TEM_TRY(vec.alloc(per * s, st));
@@ -71,7 +71,7 @@ int solve_shifts(const tem_grid* g, const double* xi, int s, const tem_options& 
   for (int i = 0; i < s; ++i) {
     SlotVectors v = carve_slot(static_cast<char*>(vec.ptr) + per * i, ncomp, opt.precision);
     const void* rc = rhs_c_dev ? static_cast<const char*>(rhs_c_dev) + (size_t)i * 3 * ncomp * 16 : nullptr;
-    TEM_TRY(batch->add_slot(g->v, xi[2 * i], xi[2 * i + 1], v, f_dev, rc));
+    TEM_TRY(batch->add_slot(g->v, xi[2 * i], xi[2 * i + 1], v, f_dev, rc, rhs_div));
   }
   TEM_TRY(batch->setup(opt, st, bnorm2));
   return batch->solve(opt, st, stats);
@@ -281,6 +281,75 @@ int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) 
   std::vector<int32_t> it;
   std::vector<double> rr;
   return collect_status(*ab, it, rr);
+}
+
+int tem_jvp(tem_state* S, const double* dlogsigma, void* cuda_stream, double* ddbzdt_out) {
+  if (!S || !dlogsigma || !ddbzdt_out || !S->batch) return TEM_EINVAL;
+  const tem_grid* grid = S->grid;
+  const int64_t ncomp = grid->v.ncomp;
+  bool any = false;
+  for (int64_t q = 0; q < ncomp; ++q) {
+    if (!std::isfinite(dlogsigma[q])) return TEM_EINVAL;
+    any = any || dlogsigma[q] != 0.0;
+  }
+  const int s = S->s, K = S->K, n_rx = S->n_rx;
+  if (!any) {
+    std::memset(ddbzdt_out, 0, (size_t)n_rx * K * sizeof(double));
+    return TEM_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  TEM_CUDA_TRY(cudaSetDevice(grid->device));
+  // right-hand sides b_i = xi_i dM x_i and their norms (fixed-order partial sums)
+  DevBuf dmb, rhs, part;
+  TEM_TRY(dmb.alloc(ncomp * sizeof(double), st));
+  TEM_TRY(rhs.alloc((size_t)s * 3 * ncomp * 16, st));
+  const int nb = 2 * 152;
+  TEM_TRY(part.alloc((size_t)s * nb * sizeof(double), st));
+  TEM_CUDA_TRY(cudaMemcpyAsync(dmb.ptr, dlogsigma, ncomp * sizeof(double), cudaMemcpyHostToDevice, st));
+  k_jvp_rhs<<<152 * 8, 256, 0, st>>>(grid->v, grid->sig.as<double>(), dmb.as<double>(), S->batch->slots_device(),
+                                      S->batch->scalars_device(), s, rhs.as<double>());
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
+  k_rhs_norm2<<<dim3(nb, s), NT, 0, st>>>(rhs.as<double>(), 3 * ncomp, part.as<double>());
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
+  std::vector<double> ph((size_t)s * nb), ww(s, 0.0);
+  TEM_CUDA_TRY(cudaMemcpyAsync(ph.data(), part.ptr, ph.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TEM_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < s; ++i) {
+    for (int b = 0; b < nb; ++b) ww[i] += ph[(size_t)i * nb + b];
+    if (ww[i] == 0.0) ww[i] = 1e-300;  // solve of a zero right-hand side ends at once
+  }
+  // the batched solves A_i dx_i = b_i (G^T b_i != 0 in general)
+  DevBuf vec;
+  std::unique_ptr<Batch> jb;
+  SolveStats stats;
+  int rc = solve_shifts(grid, S->xi.data(), s, S->opt, st, nullptr, rhs.ptr, ww.data(), vec, jb, &stats, 1);
+  if (rc != TEM_OK) return rc;
+  // dd[r, k] = sum_i Re(c_ik q_r^T dx_i)
+  const size_t nt = S->term_edge.size();
+  DevBuf misc;
+  TEM_TRY(misc.alloc(256 + nt * 16 + (n_rx + 1) * 8 + 2 * (size_t)s * K * 8 + (size_t)n_rx * K * 8, st));
+  int64_t* d_tedge = misc.as<int64_t>();
+  double* d_tw = reinterpret_cast<double*>(d_tedge + nt);
+  double* d_c = d_tw + nt;
+  double* d_out = d_c + 2 * s * K;
+  int* d_toff = reinterpret_cast<int*>(d_out + n_rx * K);
+  if (nt) {
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_tedge, S->term_edge.data(), nt * 8, cudaMemcpyHostToDevice, st));
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_tw, S->term_w.data(), nt * 8, cudaMemcpyHostToDevice, st));
+  }
+  TEM_CUDA_TRY(cudaMemcpyAsync(d_toff, S->term_off.data(), (n_rx + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  TEM_CUDA_TRY(cudaMemcpyAsync(d_c, S->c.data(), 2 * (size_t)s * K * 8, cudaMemcpyHostToDevice, st));
+  k_project_combine<<<n_rx, 128, 0, st>>>(jb->slots_device(), jb->scalars_device(), s, d_tedge, d_tw, d_toff, d_c, K,
+                                           d_out, n_rx);
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
+  TEM_CUDA_TRY(cudaMemcpyAsync(ddbzdt_out, d_out, (size_t)n_rx * K * sizeof(double), cudaMemcpyDeviceToHost, st));
+  TEM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int32_t> it;
+  std::vector<double> rr;
+  return collect_status(*jb, it, rr);
 }
 
 int tem_state_destroy(tem_state* state) {

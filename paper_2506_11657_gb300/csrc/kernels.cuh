@@ -1095,8 +1095,19 @@ __device__ __forceinline__ C2<T> div_Mv(const Geo<T>& G, const GridView& g, cons
          (G.Rz[k - 1] * G.Me[2 * nc + n - sz]) * zm - (G.Rz[k] * G.Me[2 * nc + n]) * zp;
 }
 
+// (G^T v)_n at interior node n for an FP64 complex edge field v: +v / L on the three arriving
+// edges, -v / L on the three leaving ones.
+__device__ __forceinline__ C2<double> div_v(const Geo<double>& G, const GridView& g, const void* v, int i, int j,
+                                            int k, int64_t n) {
+  const int64_t nc = g.ncomp, sy = g.nx, sz = (int64_t)g.nx * g.ny;
+  return G.Rx[i - 1] * ld<double>(v, n - 1) - G.Rx[i] * ld<double>(v, n) + G.Ry[j - 1] * ld<double>(v, nc + n - sy) -
+         G.Ry[j] * ld<double>(v, nc + n) + G.Rz[k - 1] * ld<double>(v, 2 * nc + n - sz) -
+         G.Rz[k] * ld<double>(v, 2 * nc + n);
+}
+
 // INIT: the pass that starts an armed solve (cn from x64 in FP64, d = 0); otherwise the
-// pass that ends an iteration of an active solve.
+// pass that ends an iteration of an active solve.  For a right-hand side b with G^T b != 0
+// (rhs_div) the start adds it: G^T r64 = G^T b + xi G^T M x64, so cn = s (G^T b + xi G^T M x64).
 template <class T, bool INIT>
 __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
   __shared__ double red[NT / 32 * 4];
@@ -1127,7 +1138,9 @@ __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
     if (i > 0 && j > 0 && k > 0) {
       C2<T> dv;
       if (INIT) {  // start of a solve: cn = s xi G^T M x64 in FP64; d = 0
-        const C2<double> c0 = sc * cmul(xi64, div_Mv<double, double>(G64, g, x64, nullptr, i, j, int(k), n));
+        C2<double> c0 = cmul(xi64, div_Mv<double, double>(G64, g, x64, nullptr, i, j, int(k), n));
+        if (d.rhs_div) c0 = c0 + div_v(G64, g, d.rhs_c, i, j, int(k), n);
+        c0 = sc * c0;
         dv = C2<T>(T(c0.re), T(c0.im));
         st<T>(d.cn, n, dv);
       } else {
@@ -1429,6 +1442,56 @@ static __global__ void k_gradient(GridView g, const double* sigma, const SlotDes
     }
     grad[cidx] = q * acc;
   }
+}
+
+// ------------------------------------------------- linearised forward (Sec. 4)
+// b_i[e] = xi_i dM_e x_i[e] with dM_e = sum over the four cells around edge e of
+// sigma_c dm_c V_c / 4 (the lumped mass with sigma replaced by sigma * dm); boundary and
+// padding entries 0.  b_i is stored at rhs + i * 3 * ncomp (complex).
+static __global__ void k_jvp_rhs(GridView g, const double* sigma, const double* dm, const SlotDesc* fwd,
+                                 const SlotScalars* fsc, int s, double* rhs) {
+  const int64_t nc = g.ncomp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * nc; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = int(e / nc);
+    const int64_t r = e - c * nc;
+    const int i = int(r % g.nx);
+    const int64_t r2 = r / g.nx;
+    const int j = int(r2 % g.ny), k = int(r2 / g.ny);
+    double m = 0.0;
+    if (edge_valid(c, i, j, k)) {
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          int ci = i, cj = j, ck = k;
+          if (c == 0) { cj = j - 1 + a; ck = k - 1 + b; }
+          if (c == 1) { ci = i - 1 + a; ck = k - 1 + b; }
+          if (c == 2) { ci = i - 1 + a; cj = j - 1 + b; }
+          const int64_t cell = ci + (int64_t)g.nx * (cj + (int64_t)g.ny * ck);
+          m += 0.25 * sigma[cell] * dm[cell] * g.Lx[ci] * g.Ly[cj] * g.Lz[ck];
+        }
+    }
+    for (int sh = 0; sh < s; ++sh) {
+      C2<double> b = czero<double>();
+      if (m != 0.0) {
+        const C2<double> xv = ld<double>(fwd[sh].x64[fsc[sh].xcur], e);
+        b = cmul(C2<double>(fwd[sh].xi_re * m, fwd[sh].xi_im * m), xv);
+      }
+      st<double>(rhs + (int64_t)sh * 6 * nc, e, b);
+    }
+  }
+}
+
+// Per-slot ||b_i||^2 partials: block (b, i) sums |b_i|^2 over its fixed chunk into
+// part[i * gridDim.x + b]; the host adds the partials in order.
+static __global__ void k_rhs_norm2(const double* rhs, int64_t n, double* part) {
+  __shared__ double red[NT / 32];
+  const int sh = blockIdx.y;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t e0 = (int64_t)blockIdx.x * per, e1 = e0 + per < n ? e0 + per : n;
+  const double* v = rhs + (int64_t)sh * 2 * n;
+  double acc[1] = {0.0};
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += NT) acc[0] += v[2 * e] * v[2 * e] + v[2 * e + 1] * v[2 * e + 1];
+  block_sum<1, NT>(acc, red);
+  if (threadIdx.x == 0) part[(int64_t)sh * gridDim.x + blockIdx.x] = acc[0];
 }
 
 }  // namespace tem

@@ -67,7 +67,7 @@ Batch::~Batch() {
 }
 
 int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVectors& v,
-                    const double* f_real, const void* rhs_complex) {
+                    const double* f_real, const void* rhs_complex, int rhs_div) {
   if ((int64_t)slots_h_.size() >= (1 << 20)) return TEM_EINVAL;
   SlotDesc d;
   std::memset(&d, 0, sizeof(d));
@@ -90,6 +90,7 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
   d.x64[1] = v.x64[1];
   d.f = f_real;
   d.rhs_c = static_cast<const double*>(rhs_complex);
+  d.rhs_div = rhs_complex && rhs_div ? 1 : 0;
   d.fp64_inner = precision_ == TEM_PREC_FP64 ? 1 : 0;
   d.nodal = nodal_;
   d.div_nx = make_fastdiv((uint32_t)g.nx);

@@ -28,7 +28,7 @@ class Batch {
   Batch(int precision, int nodal) : precision_(precision), nodal_(nodal) {}
   ~Batch();
   int add_slot(const GridView& g, double xi_re, double xi_im, const SlotVectors& v,
-               const double* f_real, const void* rhs_complex);
+               const double* f_real, const void* rhs_complex, int rhs_div = 0);
   int setup(const tem_options& opt, cudaStream_t st, const double* ff_per_slot);
   int solve(const tem_options& opt, cudaStream_t st, SolveStats* stats);
   // host copies after solve()

@@ -150,7 +150,8 @@ struct SlotDesc {
   FastDiv div_nx, div_ny, div_nynz;
   // defect correction (FP64 outer loop)
   const double* f;          // right-hand side, real, edge layout (FP64)
-  const double* rhs_c;      // complex right-hand side (adjoint), or NULL
+  const double* rhs_c;      // complex right-hand side (adjoint, linearised forward), or NULL
+  int rhs_div;              // 1: the right-hand side may have G^T b != 0 (linearised forward)
   void* x64[2];             // FP64 iterate, double-buffered by the residual pass
   int nodal;                // 1: preconditioner with the nodal-gradient correction; 0: Jacobi only
   int fp64_inner;           // 1: inner sweeps in FP64 (aim at the final tolerance directly)

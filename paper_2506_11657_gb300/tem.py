@@ -22,7 +22,7 @@ PRECOND_AUTO, PRECOND_JACOBI, PRECOND_NODAL = 0, 1, 2
 
 EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
-            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_state_solution", "tem_adjoint",
+            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_state_solution", "tem_adjoint", "tem_jvp",
             "tem_state_destroy", "tem_apply_operator", "tem_apply_operator_noalloc", "tem_launch_count",
             "tem_profile_passes", "tem_server_default_options", "tem_server_create", "tem_server_submit",
             "tem_server_step", "tem_server_poll", "tem_server_counts", "tem_server_destroy"]
@@ -82,6 +82,7 @@ def lib():
     L.tem_state_stats.argtypes = [C.c_void_p, _i32p, _dp]
     L.tem_state_solution.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, _dp]
     L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
+    L.tem_jvp.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
     L.tem_state_destroy.argtypes = [C.c_void_p]
     L.tem_apply_operator.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]
     L.tem_apply_operator_noalloc.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_void_p, C.c_void_p, C.c_int32,
@@ -226,6 +227,16 @@ class State:
         out = np.zeros(self.n_cells)
         rc = lib().tem_adjoint(self.handle, _ptr(g), _stream(stream), _ptr(out))
         _check(rc, "tem_adjoint", ok=(TEM_OK, TEM_ENOCONV))
+        return out
+
+    def jvp(self, dlogsigma, stream=None):
+        """J dm (tem_jvp): the linearised response (n_rx, K) along a direction in log sigma."""
+        dm = _f64(dlogsigma).ravel()
+        if dm.size != self.n_cells:
+            raise ValueError(f"jvp: {dm.size} values for {self.n_cells} cells")
+        out = np.zeros((self.n_rx, self.K))
+        rc = lib().tem_jvp(self.handle, _ptr(dm), _stream(stream), _ptr(out))
+        _check(rc, "tem_jvp", ok=(TEM_OK, TEM_ENOCONV))
         return out
 
     def close(self):
