@@ -355,12 +355,23 @@ def main():
         e1.record(stream)
         gr = rk.state.adjoint(g, stream=stream)
         e2.record(stream)
+        # all K field snapshots (the columns of S R): reads s complex FP64 and writes K FP64 per edge
+        U = torch.empty((len(model.t), 3 * model.sigma.size), dtype=torch.float64, device=dev)
+        rk.state.fields(out=U, stream=stream)
+        e3, e4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e3.record(stream)
+        rk.state.fields(out=U, stream=stream)
+        e4.record(stream)
         torch.cuda.synchronize()
         rk.state.close()
+        del U
+        fields_ms = e3.elapsed_time(e4)
+        fields_bytes = 3 * model.sigma.size * (16 * len(shifts) + 8 * len(model.t))
         lhs, rhs = float(np.sum(g * jd)), float(np.dot(gr, dm))
         derivs = {"jvp_ms": e0.elapsed_time(e1), "adjoint_ms": e1.elapsed_time(e2),
                   "forward_ms": float(np.median(step_ms)),
-                  "transpose_rel_gap": abs(lhs - rhs) / (np.sum(np.abs(g * jd)) + np.sum(np.abs(gr * dm)))}
+                  "transpose_rel_gap": abs(lhs - rhs) / (np.sum(np.abs(g * jd)) + np.sum(np.abs(gr * dm))),
+                  "fields_ms_all_channels": fields_ms, "fields_gbs": fields_bytes / (fields_ms * 1e-3) / 1e9}
 
     # per-kernel timing of the passes (dominant kernel roofline)
     prof = tem.profile_passes(grid, model.loop_xy, model.z_loop, shifts, tem.PREC_MIXED, n_iter=20, stream=stream)

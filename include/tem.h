@@ -202,6 +202,16 @@ int tem_state_stats(const tem_state* state, int32_t* iters, double* relres);
 int tem_state_solution(const tem_state* state, int64_t i, void* cuda_stream, double* x_out);
 
 /*
+ * Time snapshots of the field, the columns of S R in Sec. 3.2: for the channels
+ * k = k0 .. k0+nk-1 writes u_k[e] = sum_i Re(c[i, k] x_i[e]) (Eq. (rmj) on every edge: the
+ * rational approximation of exp(-t_k M^{-1} K) M^{-1} f) to u_dev, caller-owned DEVICE memory of
+ * nk * 3 * nx*ny*nz doubles, channel-major, each channel in the edge layout of
+ * tem_state_solution.  Enqueued on cuda_stream, not synchronised.  TEM_EINVAL for NULL
+ * pointers or a channel range outside [0, K).
+ */
+int tem_state_fields(const tem_state* state, int64_t k0, int64_t nk, void* cuda_stream, void* u_dev);
+
+/*
  * Adjoint gradient (Sec. 4): given g = dphi/dd (host, n_rx*K doubles laid
  * out like dbzdt_out), writes grad[c] = dphi/dlog sigma_c for every cell
  * (host, nx*ny*nz doubles):

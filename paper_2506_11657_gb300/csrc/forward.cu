@@ -204,6 +204,23 @@ int tem_state_solution(const tem_state* state, int64_t i, void* cuda_stream, dou
   return TEM_OK;
 }
 
+int tem_state_fields(const tem_state* state, int64_t k0, int64_t nk, void* cuda_stream, void* u_dev) {
+  if (!state || !u_dev || !state->batch || k0 < 0 || nk < 1 || k0 + nk > state->K) return TEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  TEM_CUDA_TRY(cudaSetDevice(state->grid->device));
+  DevBuf cb;
+  TEM_TRY(cb.alloc(state->c.size() * sizeof(double), st));
+  TEM_CUDA_TRY(cudaMemcpyAsync(cb.ptr, state->c.data(), state->c.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  const int64_t n3 = 3 * state->grid->v.ncomp;
+  const int64_t nblk = ((n3 + NT - 1) / NT) * nk;
+  if (nblk > 2147483647LL) return TEM_EINVAL;
+  k_fields<<<(unsigned)nblk, NT, 0, st>>>(state->batch->slots_device(), state->batch->scalars_device(), state->s,
+                                     cb.as<double>(), state->K, int(k0), int(nk), n3, static_cast<double*>(u_dev));
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
+  return TEM_OK;
+}
+
 int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) {
   if (!S || !g || !grad || !S->batch) return TEM_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -1444,6 +1444,32 @@ static __global__ void k_gradient(GridView g, const double* sigma, const SlotDes
   }
 }
 
+// ------------------------------------------------- time snapshots of the field (Sec. 3.2)
+// The columns of S R: u_k[e] = sum_i Re(c[i, k] x_i[e]) for k = k0 .. k0+nk-1, stored at
+// out + (k - k0) * n3.  One thread per (edge, channel); the channel varies fastest over the
+// blocks, so the nk blocks of one edge range run together and read the x_i of their range
+// from L2 after the first of them brought it in: HBM sees x once and every output once.
+static __global__ void __launch_bounds__(NT) k_fields(const SlotDesc* slots, const SlotScalars* sc, int s,
+                                                      const double* c, int K, int k0, int nk, int64_t n3,
+                                                      double* out) {
+  __shared__ const double2* xp[64];
+  __shared__ double2 cs[64];
+  const int kk = int(blockIdx.x % (unsigned)nk);
+  const int64_t e = (int64_t)(blockIdx.x / (unsigned)nk) * NT + threadIdx.x;
+  for (int i = threadIdx.x; i < s; i += NT) {
+    xp[i] = static_cast<const double2*>(slots[i].x64[sc[i].xcur]);
+    cs[i] = make_double2(c[2 * (i * K + k0 + kk)], c[2 * (i * K + k0 + kk) + 1]);
+  }
+  __syncthreads();
+  if (e >= n3) return;
+  double acc = 0.0;
+  for (int i = 0; i < s; ++i) {
+    const double2 x = xp[i][e];
+    acc += cs[i].x * x.x - cs[i].y * x.y;
+  }
+  __stcs(out + (int64_t)kk * n3 + e, acc);
+}
+
 // ------------------------------------------------- linearised forward (Sec. 4)
 // b_i[e] = xi_i dM_e x_i[e] with dM_e = sum over the four cells around edge e of
 // sigma_c dm_c V_c / 4 (the lumped mass with sigma replaced by sigma * dm); boundary and

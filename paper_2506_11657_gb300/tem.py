@@ -22,7 +22,7 @@ PRECOND_AUTO, PRECOND_JACOBI, PRECOND_NODAL = 0, 1, 2
 
 EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
-            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_state_solution", "tem_adjoint", "tem_jvp",
+            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_state_solution", "tem_state_fields", "tem_adjoint", "tem_jvp",
             "tem_state_destroy", "tem_apply_operator", "tem_apply_operator_noalloc", "tem_launch_count",
             "tem_profile_passes", "tem_server_default_options", "tem_server_create", "tem_server_submit",
             "tem_server_step", "tem_server_poll", "tem_server_counts", "tem_server_destroy"]
@@ -81,6 +81,7 @@ def lib():
                               C.c_int64, C.c_int64, C.POINTER(Options), C.c_void_p, _dp, C.POINTER(C.c_void_p)]
     L.tem_state_stats.argtypes = [C.c_void_p, _i32p, _dp]
     L.tem_state_solution.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, _dp]
+    L.tem_state_fields.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
     L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
     L.tem_jvp.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
     L.tem_state_destroy.argtypes = [C.c_void_p]
@@ -227,6 +228,19 @@ class State:
         out = np.zeros(self.n_cells)
         rc = lib().tem_adjoint(self.handle, _ptr(g), _stream(stream), _ptr(out))
         _check(rc, "tem_adjoint", ok=(TEM_OK, TEM_ENOCONV))
+        return out
+
+    def fields(self, k0=0, nk=None, out=None, stream=None):
+        """Field snapshots u_k = sum_i Re(c[i, k] x_i) for channels k0 .. k0+nk-1 (tem_state_fields),
+        as a (nk, 3 * n_cells) float64 CUDA tensor in the library's edge layout."""
+        import torch
+        nk = self.K - k0 if nk is None else nk
+        if out is None:
+            out = torch.empty((nk, 3 * self.n_cells), dtype=torch.float64, device="cuda")
+        if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous() or out.numel() < nk * 3 * self.n_cells:
+            raise ValueError("fields: out must be a contiguous float64 CUDA tensor of nk * 3 * n_cells values")
+        _check(lib().tem_state_fields(self.handle, int(k0), int(nk), _stream(stream), C.c_void_p(out.data_ptr())),
+               "tem_state_fields")
         return out
 
     def jvp(self, dlogsigma, stream=None):

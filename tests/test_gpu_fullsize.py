@@ -9,7 +9,9 @@ size, so the checks use what holds at any size:
   d[r, k] = sum_i Re(c[i, k] q_r^T x_i) with the oracle's receiver rows, to 1e-12 S_k,
   S_k = sum_i |c[i, k] q_r^T x_i|;
 * the mixed-precision response agrees with the all-FP64 path on the same model per channel
-  within 1e-5 |d| + 1e-9 S_k (the mixed bound of the small-model parity tests).
+  within 1e-5 |d| + 1e-9 S_k (the mixed bound of the small-model parity tests);
+* the field snapshots of the first and last channel project onto the response:
+  q_r^T u_k = d[r, k] to 1e-12 S_k.
 """
 import numpy as np
 import pytest
@@ -33,16 +35,18 @@ def run():
                       keep_state=True)
     assert res.status == tem.TEM_OK
     xs = [res.state.solution(i) for i in range(len(shifts))]
+    K = len(m.t)
+    U = np.stack([res.state.fields(k, 1).cpu().numpy()[0] for k in (0, K - 1)])
     res.state.close()
     d64 = tem.forward(grid, m.loop_xy, m.z_loop, m.rx, shifts, c, tem.default_options(precision="fp64")).d
     grid.close()
     P = TEMProblem(m.hx, m.hy, m.hz, m.sigma, m.loop_xy, m.z_loop, m.rx, origin=m.origin)
     idx = lib_index_of_interior(P.grid)
-    return m, shifts, c, res.d, d64, xs, P, idx
+    return m, shifts, c, res.d, d64, xs, P, idx, U
 
 
 def test_solutions_solve_the_oracle_system(run):
-    m, shifts, c, d, d64, xs, P, idx = run
+    m, shifts, c, d, d64, xs, P, idx, U = run
     pad = np.ones(xs[0].size, dtype=bool)
     pad[idx] = False
     nf = np.linalg.norm(P.f)
@@ -55,7 +59,7 @@ def test_solutions_solve_the_oracle_system(run):
 
 
 def test_response_is_the_oracle_combination(run):
-    m, shifts, c, d, d64, xs, P, idx = run
+    m, shifts, c, d, d64, xs, P, idx, U = run
     y = np.stack([P.Q @ x[idx] for x in xs])                      # (s, n_rx)
     d_ref = np.einsum("ik,ir->rk", c, y).real
     S = np.einsum("ik,ir->rk", np.abs(c), np.abs(y))
@@ -63,7 +67,16 @@ def test_response_is_the_oracle_combination(run):
 
 
 def test_mixed_agrees_with_fp64_path(run):
-    m, shifts, c, d, d64, xs, P, idx = run
+    m, shifts, c, d, d64, xs, P, idx, U = run
     y = np.stack([P.Q @ x[idx] for x in xs])
     S = np.einsum("ik,ir->rk", np.abs(c), np.abs(y))
     assert np.all(np.abs(d - d64) <= 1e-5 * np.abs(d64) + 1e-9 * S)
+
+
+def test_snapshots_project_onto_the_response(run):
+    m, shifts, c, d, d64, xs, P, idx, U = run
+    y = np.stack([P.Q @ x[idx] for x in xs])
+    S = np.einsum("ik,ir->rk", np.abs(c), np.abs(y))
+    K = len(m.t)
+    for row, k in enumerate((0, K - 1)):
+        assert np.all(np.abs(P.Q @ U[row, idx] - d[:, k]) <= 1e-12 * S[:, k] + 1e-300), k

@@ -103,3 +103,29 @@ def test_default_options_and_struct_layout(lib):
     assert (o.precision, o.max_iter, o.tol, o.inner_tol) == (lib.PREC_FP64, 20000, 1e-12, 1e-3)
     assert (o.max_outer, o.check_every, o.keep_state, o.precond, o.carry_direction) == (40, 32, 0, 0, 0)
     assert C.sizeof(o) == 48
+
+
+def test_late_time_weights_match_the_oracle_and_help_late_channels(lib):
+    """Weights w_k = (t_k / t_K)^(5/2) (the late-time decay of Sec. 5.2): the C++ and oracle
+    fitters agree, and the weighted family is far more accurate on the last channel than the
+    unweighted one (at the cost of the first)."""
+    from oracle import rational as R
+    t = np.logspace(-5, -2, 31)
+    w = (t / t[-1]) ** 2.5
+    sh, c, err = lib.poles_residues(t, 20, w)
+    sh2, c2, err2 = R.tem_poles_residues(t, 20, w=w)
+    order = [int(np.argmin(np.abs(sh2 - z))) for z in sh]
+    assert np.max(np.abs(sh - sh2[order]) / np.abs(sh2[order])) < 1e-4
+    assert abs(err - err2) <= 0.01 * err2
+
+    def per_channel(shifts, cc):
+        tau, tm = t / t[-1], t[-1]
+        x = np.concatenate([[0.0], np.logspace(-4, np.log10(1e4 / tau[0]), 20000)])
+        r = np.real(np.sum(cc[:, None, :] * tm / (x[None, :, None] - (shifts * tm)[:, None, None]), axis=0))
+        return np.abs(np.exp(-np.outer(x, tau)) - r).max(axis=0)
+
+    e_w = per_channel(sh, c)
+    e_u = per_channel(*lib.poles_residues(t, 20)[:2])
+    assert e_w[-1] < 1e-2 * e_u[-1]
+    assert e_w[0] > e_u[0]
+    assert np.max(w * e_w) <= 1.01 * err
