@@ -1,6 +1,6 @@
 """Build the TEM C-ABI library (libtem.so) in-tree for sm_103a.
 
-Every translation unit compiles in parallel with nvcc (-gencode
+Every translation unit compiles in parallel with nvcc at -O3 (-gencode
 arch=compute_103a,code=sm_103a -lineinfo); the objects link into
 ``paper_2506_11657_gb300/libtem.so`` next to this file.  No cmake.
 """
@@ -31,10 +31,9 @@ def _compile(src, nvcc, extra):
     obj = os.path.join(BUILD, src + ".o")
     path = os.path.join(CSRC, src)
     if src.endswith(".cu"):
-        cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
-               "--expt-relaxed-constexpr", *extra, "-c", path, "-o", obj]
+        cmd = [nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", *extra, "-c", path, "-o", obj]
     else:
-        cmd = [nvcc, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", *extra, "-c", path, "-o", obj]
+        cmd = [nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", *extra, "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
