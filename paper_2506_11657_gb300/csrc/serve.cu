@@ -210,7 +210,7 @@ struct tem_server {
       S.scale = 1.0 / std::sqrt(ff);
       S.inv_scale_prev = 1.0;
       S.max_outer = opt.solver.max_outer;
-      S.stall_window = 400;
+      S.stall_window = TEM_STALL_WINDOW;
       S.carry = opt.solver.carry_direction != 0;
       S.stalled = 0;
       S.carry_ratio = 0.0;

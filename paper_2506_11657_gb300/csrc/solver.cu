@@ -136,7 +136,7 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
     S.scale = 1.0 / std::sqrt(ff[q]);
     S.inv_scale_prev = 1.0;
     S.max_outer = opt.max_outer;
-    S.stall_window = 400;
+    S.stall_window = TEM_STALL_WINDOW;
     S.carry = opt.carry_direction != 0;
     S.stalled = 0;
     S.carry_ratio = 0.0;

@@ -70,4 +70,10 @@ void count_launch(int n = 1);
 void decompose_slot(SlotDesc& d, int nodal);
 constexpr int kMaxBlocksPerSlot = 4096;
 
+// An FP32 inner solve whose recursive residual has not reached a new minimum for this many
+// iterations ends, and the FP64 outer step restarts from the true residual.
+#ifndef TEM_STALL_WINDOW
+#define TEM_STALL_WINDOW 400
+#endif
+
 }  // namespace tem
