@@ -6,7 +6,7 @@ residual of 1e-12, receiver projection and pole -> channel combination) with the
 conductivity and edge mass resident in HBM and the shared poles cached (they depend only on
 the channel times and the degree).  The timed region holds exactly --steps forward models,
 bracketed by a barrier and a device synchronisation, timed with CUDA events on the launching
-stream; the working set (10 shifts x 6.4M edges, ~4.5 GB) is far larger than L2.
+stream; the working set (10 shifts x 6.4M edges, ~5.7 GB) is far larger than L2.
 
 Extra keys: the FP64 path's models/s on the same model and its per-channel agreement with the
 mixed path, per-step p50/p99, an end-to-end number through the C ABI from host buffers,
@@ -118,6 +118,17 @@ class ClockSampler:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+DATA = ("synthetic: seeded random-block conductivity (10 m cells, 8^3-cell blocks with "
+        "log10 rho ~ U[0, 3], air on top), 200 m square loop, receiver at its centre")
+
+
+def _config(workload, nside, model, n_shifts):
+    """The workload both arms report: grid, poles, channels and the stopping rule."""
+    return {"workload": workload, "grid": [nside] * 3, "cells_m": 10.0, "shifts": n_shifts,
+            "degree": model.degree, "channels": len(model.t), "t_range_s": [float(f"{model.t[0]:.6g}"), float(f"{model.t[-1]:.6g}")],
+            "tol": 1e-12, "l2": "working set ~5.7 GB at 128^3 >> L2 (no flush needed)"}
 
 
 def _kernel_sha():
@@ -232,8 +243,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "randblock128", "grid": [128, 128, 128], "shifts": len(shifts),
-                                            "channels": len(model.t), "sample": "bounded"},
+            "data": DATA, "config": _config("randblock128", 128, model, len(shifts)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": wall}
@@ -416,11 +426,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-                "data": "synthetic (seeded random-block conductivity, BASELINE config 3 shape)",
-                "config": {"workload": args.workload, "grid": [nside] * 3, "cells_m": 10.0, "shifts": len(shifts),
-                           "degree": model.degree, "channels": len(model.t), "t_range_s": [1e-5, 1e-2],
-                           "precision": "mixed", "tol": 1e-12, "uniform_err": uerr,
-                           "l2": "working set ~4.5 GB >> L2 (no flush needed)"},
+                "data": DATA, "config": _config(args.workload, nside, model, len(shifts)),
+                "fit_uniform_err": uerr,
                 "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                 "iters_per_shift_mixed": iters_mixed.tolist(), "relres_mixed": relres_mixed.tolist(),
                 "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
