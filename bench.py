@@ -418,8 +418,8 @@ def main():
     serving = run_serving_sample(args.serve_requests, stream) if args.serve_requests > 0 else None
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        v, secs, desc = cpu_oracle_sample(model, shifts, ORACLE_ITERS_128 if nside == 128 else iters_mixed)
+    if rank == 0 and not args.no_cpu_baseline and nside == 128:   # the iteration counts are for 128^3
+        v, secs, desc = cpu_oracle_sample(model, shifts, ORACLE_ITERS_128)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": secs}
 
     if rank == 0:
