@@ -4,6 +4,7 @@ geometry would cancel out):
 
 * a small grid with random widths in x, y and z and a blocky earth, FP64 and mixed, against
   the oracle's sparse-LU response with the per-channel bound of the forward tests;
+* the adjoint gradient and J dm on the random-width grid against the oracle (FP64);
 * the padded layered model (48^3 core of 10 m cells, 8 padding cells growing by 1.15 on every
   side), mixed precision as the benchmark runs it: every FP64 solution solves the oracle's own
   assembled system to 1e-11 and the response is the oracle's combination of the solutions.
@@ -82,3 +83,24 @@ def test_padded_layered_model_solves_the_oracle_system():
     d_ref = np.einsum("ik,ir->rk", c, y).real
     S = np.einsum("ik,ir->rk", np.abs(c), np.abs(y))
     assert np.all(np.abs(res.d - d_ref) <= 1e-12 * S + 1e-300)
+
+
+def test_random_widths_adjoint_and_jvp_match_oracle(small):
+    """The adjoint gradient and J dm weight by sigma_c V_c / 4 with per-axis widths: both against
+    the oracle (FP64 solves to 1e-13), relative to their largest entries."""
+    from paper_2506_11657_gb300 import tem
+    m, shifts, c, d, S = small
+    P = TEMProblem(m.hx, m.hy, m.hz, m.sigma, m.loop_xy, m.z_loop, m.rx, origin=m.origin)
+    _, xs = P.forward(shifts, c, return_solutions=True)
+    rng = np.random.default_rng(52)
+    g = rng.standard_normal(d.shape) / np.abs(d).mean()
+    dm = rng.standard_normal(m.sigma.size) * (m.sigma.ravel() > 1e-6)
+    grad_ref = P.adjoint_gradient(shifts, c, g, xs=xs)
+    jd_ref = P.jvp(shifts, c, dm, xs=xs)
+    grid = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma)
+    res = tem.forward(grid, m.loop_xy, m.z_loop, m.rx, shifts, c, tem.default_options(tol=1e-13), keep_state=True)
+    grad = res.state.adjoint(g)
+    jd = res.state.jvp(dm)
+    res.state.close()
+    assert np.abs(grad - grad_ref).max() <= 1e-7 * np.abs(grad_ref).max()
+    assert np.abs(jd - jd_ref).max() <= 1e-7 * np.abs(jd_ref).max()
