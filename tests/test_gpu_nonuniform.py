@@ -33,7 +33,10 @@ def _random_width_model():
     _, yn = W._centres(hy, origin[1])
     sigma = W._block_sigma(nz, ny, nx, air, 4, rng, (0.5, 2.5))
     loop = W._square_loop(60.0, xn, yn)
-    rx = np.array([[0.0, 0.0, 0.0], [xn[nx // 2 + 3], yn[ny // 2 - 2], 0.0], [xn[3], yn[ny - 4], 0.0]])
+    # two receivers on nodes, two between nodes (bilinear weights over unequal z faces)
+    rx = np.array([[0.0, 0.0, 0.0], [xn[nx // 2 + 3], yn[ny // 2 - 2], 0.0], [xn[3], yn[ny - 4], 0.0],
+                   [0.37 * xn[nx // 2 + 2] + 0.63 * xn[nx // 2 + 3], 0.8 * yn[ny // 2 - 3] + 0.2 * yn[ny // 2 - 2], 0.0],
+                   [0.5 * (xn[2] + xn[3]), 0.25 * yn[ny - 5] + 0.75 * yn[ny - 4], 0.0]])
     return W.Model("randwidth", hx, hy, hz, origin, sigma, loop, 0.0, rx, W.channel_times(1e-5, 1e-2, 10), 12)
 
 
