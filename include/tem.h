@@ -184,6 +184,24 @@ int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
                 tem_state** state_out);
 
 /*
+ * Several loop sources on one grid in one batched solve (the block source f of Sec. 4, "Using
+ * multiple sources"): source j is the closed polygon loops_xy[2 * vert_off[j] .. 2 * vert_off[j+1])
+ * (x, y pairs, at least 3 vertices) at height z_loops[j] carrying currents[j]; all sources share
+ * the receivers rx_xyz, the shifts xi and the channel weights c (same meaning as tem_forward).
+ * The n_src * s shifted systems advance together, one launch per pass for all of them; each
+ * system's arithmetic depends only on its own data, so the result equals n_src separate
+ * tem_forward calls bit for bit.  dbzdt_out (host, caller-owned) holds n_src * n_rx * K
+ * doubles, source-major, each source's block laid out like tem_forward's output.
+ * 1 <= n_src <= 1024; opt->keep_state must be 0 (no state is kept).  Returns TEM_EINVAL for
+ * bad sizes, loops or receivers (before any device work), TEM_ENOCONV (output written),
+ * TEM_EBREAKDOWN, TEM_ENOMEM or TEM_ECUDA.
+ */
+int tem_forward_sources(const tem_grid* grid, const double* loops_xy, const int64_t* vert_off, int64_t n_src,
+                        const double* z_loops, const double* currents, const double* rx_xyz, int64_t n_rx,
+                        const double* xi, const double* c, int64_t s, int64_t K, const tem_options* opt,
+                        void* cuda_stream, double* dbzdt_out);
+
+/*
  * Per-shift diagnostics of the last forward (or adjoint) solve kept in `state`:
  *   iters[s]   : COCG iterations (inner FP32 iterations summed, for MIXED),
  *   relres[s]  : final FP64 relative residual ||f - A_i x_i|| / ||f||.

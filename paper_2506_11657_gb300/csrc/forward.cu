@@ -184,6 +184,112 @@ int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
   return rc;
 }
 
+int tem_forward_sources(const tem_grid* grid, const double* loops_xy, const int64_t* vert_off, int64_t n_src,
+                        const double* z_loops, const double* currents, const double* rx_xyz, int64_t n_rx,
+                        const double* xi, const double* c, int64_t s, int64_t K, const tem_options* opt_in,
+                        void* cuda_stream, double* dbzdt_out) {
+  if (!grid || !loops_xy || !vert_off || !z_loops || !currents || !rx_xyz || !dbzdt_out) return TEM_EINVAL;
+  if (n_src < 1 || n_src > 1024 || n_rx < 1 || n_rx > 4096) return TEM_EINVAL;
+  tem_options opt;
+  tem_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.keep_state) return TEM_EINVAL;
+  TEM_TRY(validate_options(opt));
+  TEM_TRY(validate_poles(xi, c, s, K));
+  if (vert_off[0] != 0) return TEM_EINVAL;
+  for (int64_t j = 0; j < n_src; ++j)
+    if (vert_off[j + 1] - vert_off[j] < 3) return TEM_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  TEM_CUDA_TRY(cudaSetDevice(grid->device));
+  // sources and receivers (sparse term lists, host); validated before any device work
+  std::vector<std::vector<Term>> fterms(n_src);
+  for (int64_t j = 0; j < n_src; ++j)
+    TEM_TRY(build_source(grid, loops_xy + 2 * vert_off[j], vert_off[j + 1] - vert_off[j], z_loops[j], currents[j],
+                         fterms[j]));
+  std::vector<int64_t> term_edge;
+  std::vector<double> term_w;
+  std::vector<int> term_off(1, 0);
+  for (int64_t r = 0; r < n_rx; ++r) {
+    std::vector<Term> q;
+    TEM_TRY(build_receiver(grid, rx_xyz + 3 * r, q));
+    for (auto& t : q) {
+      term_edge.push_back(t.edge);
+      term_w.push_back(t.w);
+    }
+    term_off.push_back((int)term_edge.size());
+  }
+  const int64_t ncomp = grid->v.ncomp;
+  const size_t nt = term_edge.size();
+  // one dense real source vector per loop
+  DevBuf fbuf, misc, vec;
+  TEM_TRY(fbuf.alloc((size_t)n_src * 3 * ncomp * sizeof(double), st));
+  TEM_CUDA_TRY(cudaMemsetAsync(fbuf.ptr, 0, (size_t)n_src * 3 * ncomp * sizeof(double), st));
+  size_t nf = 0;
+  for (auto& ft : fterms) nf += ft.size();
+  const size_t misc_bytes = 256 + nf * 16 + nt * 16 + (n_rx + 1) * 8 + 2 * s * K * 8 + (size_t)n_src * n_rx * K * 8;
+  TEM_TRY(misc.alloc(misc_bytes, st));
+  int64_t* d_fidx = misc.as<int64_t>();
+  double* d_fval = reinterpret_cast<double*>(d_fidx + nf);
+  int64_t* d_tedge = reinterpret_cast<int64_t*>(d_fval + nf);
+  double* d_tw = reinterpret_cast<double*>(d_tedge + nt);
+  double* d_c = d_tw + nt;
+  double* d_out = d_c + 2 * s * K;
+  int* d_toff = reinterpret_cast<int*>(d_out + (size_t)n_src * n_rx * K);
+  std::vector<double> ffs;
+  {
+    std::vector<int64_t> fi;
+    std::vector<double> fv;
+    for (int64_t j = 0; j < n_src; ++j) {
+      double ff = 0.0;
+      for (auto& t : fterms[j]) {
+        fi.push_back(j * 3 * ncomp + t.edge);
+        fv.push_back(t.w);
+        ff += t.w * t.w;
+      }
+      for (int64_t i = 0; i < s; ++i) ffs.push_back(ff);
+    }
+    if (!fi.empty()) {
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_fidx, fi.data(), fi.size() * 8, cudaMemcpyHostToDevice, st));
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_fval, fv.data(), fv.size() * 8, cudaMemcpyHostToDevice, st));
+      k_scatter<<<(int)((fi.size() + 255) / 256 + 1), 256, 0, st>>>(d_fidx, d_fval, (int64_t)fi.size(),
+                                                                     fbuf.as<double>());
+      count_launch();
+      TEM_CUDA_TRY(cudaGetLastError());
+    }
+    if (nt) {
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_tedge, term_edge.data(), nt * 8, cudaMemcpyHostToDevice, st));
+      TEM_CUDA_TRY(cudaMemcpyAsync(d_tw, term_w.data(), nt * 8, cudaMemcpyHostToDevice, st));
+    }
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_toff, term_off.data(), (n_rx + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+    TEM_CUDA_TRY(cudaMemcpyAsync(d_c, c, 2 * s * K * 8, cudaMemcpyHostToDevice, st));
+  }
+  // all n_src * s systems in one batch: slot j * s + i is source j, shift i
+  const size_t per = slot_vector_bytes(ncomp, opt.precision);
+  TEM_TRY(vec.alloc(per * n_src * s, st));
+  Batch b(opt.precision, use_nodal(opt));
+  for (int64_t j = 0; j < n_src; ++j)
+    for (int64_t i = 0; i < s; ++i)
+      TEM_TRY(b.add_slot(grid->v, xi[2 * i], xi[2 * i + 1],
+                         carve_slot(vec.as<char>() + per * (j * s + i), ncomp, opt.precision),
+                         fbuf.as<double>() + j * 3 * ncomp, nullptr));
+  TEM_TRY(b.setup(opt, st, ffs.data()));
+  SolveStats stats;
+  TEM_TRY(b.solve(opt, st, &stats));
+  for (int64_t j = 0; j < n_src; ++j) {
+    k_project_combine<<<(int)n_rx, 128, 0, st>>>(b.slots_device() + j * s, b.scalars_device() + j * s, int(s),
+                                                   d_tedge, d_tw, d_toff, d_c, int(K), d_out + j * n_rx * K,
+                                                   int(n_rx));
+    count_launch();
+    TEM_CUDA_TRY(cudaGetLastError());
+  }
+  TEM_CUDA_TRY(cudaMemcpyAsync(dbzdt_out, d_out, (size_t)n_src * n_rx * K * sizeof(double), cudaMemcpyDeviceToHost,
+                               st));
+  TEM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<int32_t> it;
+  std::vector<double> rr;
+  return collect_status(b, it, rr);
+}
+
 int tem_state_stats(const tem_state* state, int32_t* iters, double* relres) {
   if (!state) return TEM_EINVAL;
   for (int i = 0; i < state->s; ++i) {

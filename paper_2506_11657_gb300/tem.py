@@ -22,7 +22,7 @@ PRECOND_AUTO, PRECOND_JACOBI, PRECOND_NODAL = 0, 1, 2
 
 EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
-            "tem_poles_residues", "tem_forward", "tem_state_stats", "tem_state_solution", "tem_state_fields", "tem_adjoint", "tem_jvp",
+            "tem_poles_residues", "tem_forward", "tem_forward_sources", "tem_state_stats", "tem_state_solution", "tem_state_fields", "tem_adjoint", "tem_jvp",
             "tem_state_destroy", "tem_apply_operator", "tem_apply_operator_noalloc", "tem_launch_count",
             "tem_profile_passes", "tem_server_default_options", "tem_server_create", "tem_server_submit",
             "tem_server_step", "tem_server_poll", "tem_server_counts", "tem_server_destroy"]
@@ -80,6 +80,8 @@ def lib():
     L.tem_forward.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, _dp, _dp,
                               C.c_int64, C.c_int64, C.POINTER(Options), C.c_void_p, _dp, C.POINTER(C.c_void_p)]
     L.tem_state_stats.argtypes = [C.c_void_p, _i32p, _dp]
+    L.tem_forward_sources.argtypes = [C.c_void_p, _dp, _i64p, C.c_int64, _dp, _dp, _dp, C.c_int64, _dp, _dp,
+                                      C.c_int64, C.c_int64, C.POINTER(Options), C.c_void_p, _dp]
     L.tem_state_solution.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, _dp]
     L.tem_state_fields.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
     L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
@@ -291,6 +293,29 @@ def forward(grid: Grid, loop_xy, z_loop, rx, shifts, c, options: Options | None 
     _check(rc, "tem_forward", ok=(TEM_OK, TEM_ENOCONV))
     st = State(h, s, len(rxa), K, int(np.prod(grid.shape))) if (keep_state and h.value) else None
     return ForwardResult(out, rc, st)
+
+
+def forward_sources(grid: Grid, loops, z_loops, rx, shifts, c, options: Options | None = None, currents=None,
+                    stream=None):
+    """tem_forward_sources: d_t b_z (n_src, n_rx, K) for several loops solved as one batch.
+    loops: sequence of (n_j, 2) vertex arrays; z_loops, currents: one value per loop."""
+    loops = [_f64(l).reshape(-1, 2) for l in loops]
+    n_src = len(loops)
+    verts = np.ascontiguousarray(np.concatenate(loops), dtype=np.float64)
+    off = np.ascontiguousarray(np.concatenate(([0], np.cumsum([len(l) for l in loops]))), dtype=np.int64)
+    zl = _f64(np.broadcast_to(np.asarray(z_loops, dtype=np.float64), (n_src,)))
+    cur = _f64(np.ones(n_src) if currents is None else np.broadcast_to(np.asarray(currents, np.float64), (n_src,)))
+    rxa = _f64(rx).reshape(-1, 3)
+    shifts = np.ascontiguousarray(shifts, dtype=np.complex128)
+    cc = np.ascontiguousarray(c, dtype=np.complex128)
+    s, K = cc.shape
+    opt = options or default_options()
+    out = np.zeros((n_src, len(rxa), K))
+    rc = lib().tem_forward_sources(grid.handle, _ptr(verts), off.ctypes.data_as(_i64p), n_src, _ptr(zl), _ptr(cur),
+                                   _ptr(rxa), len(rxa), _ptr(shifts.view(np.float64)), _ptr(cc.view(np.float64).ravel()),
+                                   s, K, C.byref(opt), _stream(stream), _ptr(out))
+    _check(rc, "tem_forward_sources", ok=(TEM_OK, TEM_ENOCONV))
+    return out
 
 
 def apply_operator(grid: Grid, shifts, p, q, precision=PREC_FP64, stream=None):
