@@ -111,3 +111,26 @@ def test_jvp_is_the_transpose_of_the_adjoint():
     lhs = np.sum(g * P.jvp(sh, c, dm, xs=xs))
     rhs = np.dot(P.adjoint_gradient(sh, c, g, xs=xs), dm)
     assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + abs(rhs))
+
+
+def test_jvp_on_random_widths_matches_finite_differences():
+    """J dm on a grid of unequal cell widths against central differences of the forward."""
+    rng = np.random.default_rng(13)
+    nx, ny, nz, air = 6, 5, 7, 2
+    hx, hy, hz = rng.uniform(10, 30, nx), rng.uniform(10, 30, ny), rng.uniform(10, 30, nz)
+    xn = np.concatenate(([0.0], np.cumsum(hx))) - hx[:3].sum()
+    yn = np.concatenate(([0.0], np.cumsum(hy))) - hy[:2].sum()
+    origin = (-hx[:3].sum(), -hy[:2].sum(), -hz[:nz - air].sum())
+    sigma = np.full((nz, ny, nx), 1e-8)
+    sigma[:nz - air] = 10 ** rng.uniform(-2.5, -1.0, (nz - air, ny, nx))
+    loop = np.array([[xn[2], yn[1]], [xn[4], yn[1]], [xn[4], yn[3]], [xn[2], yn[3]]])
+    rx = np.array([[xn[3], yn[2], 0.0], [0.5 * (xn[1] + xn[2]), 0.3 * yn[3] + 0.7 * yn[4], 0.0]])
+    t = np.logspace(-5, -3, 6)
+    sh, c, _ = R.tem_poles_residues(t, 8)
+    P = TEMProblem(hx, hy, hz, sigma, loop, 0.0, rx, origin=origin)
+    dm = rng.standard_normal(sigma.size) * (sigma.ravel() > 1e-6)
+    jd = P.jvp(sh, c, dm)
+    h = 1e-4
+    dp = TEMProblem(hx, hy, hz, sigma.ravel() * np.exp(h * dm), loop, 0.0, rx, origin=origin).forward(sh, c)
+    dn = TEMProblem(hx, hy, hz, sigma.ravel() * np.exp(-h * dm), loop, 0.0, rx, origin=origin).forward(sh, c)
+    assert np.abs((dp - dn) / (2 * h) - jd).max() <= 1e-6 * np.abs(jd).max()

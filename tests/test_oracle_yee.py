@@ -157,3 +157,12 @@ def test_rejects_bad_geometry():
         g.loop_source([[0.0, 0.0], [2.0, 1.0], [0.0, 2.0]], 1.0)
     with pytest.raises(ValueError):
         g.receiver_row(5.0, 1.0, 1.0)
+
+
+def test_mass_derivative_sums_to_the_mass():
+    """dM/dlog sigma_c = diag(D[:, c]) and M is linear in sigma, so sum_c D[:, c] = M, on any widths."""
+    g = _nonuniform_grid(8)
+    rng = np.random.default_rng(9)
+    sigma = 10 ** rng.uniform(-3, 0, g.nx * g.ny * g.nz)
+    D = g.mass_derivative(sigma)
+    assert np.allclose(D @ np.ones(D.shape[1]), g.mass(sigma), rtol=1e-13, atol=0)
