@@ -509,6 +509,20 @@ extern "C" int tem_poles_residues(const double* t, int64_t K, int64_t degree, co
     }
   }
   if (bestA.empty()) return TEM_EINVAL;
+  // The poles must stay off [0, inf), the spectrum of M^{-1} K (Sec. 3.2).  A fit that has
+  // saturated (uniform error near rounding) can leave spurious real poles there, doublets
+  // with residues at rounding level: drop them and refit the residues on the others.
+  {
+    std::vector<double> keep;
+    for (double r : bestP.real)
+      if (r < 0.0) keep.push_back(r);
+    if (keep.size() != bestP.real.size()) {
+      bestP.real = keep;
+      if (bestP.upper.empty() && bestP.real.empty()) return TEM_EINVAL;
+      bestA.clear();
+      fit_residues(x, tau, bestP, bestA);
+    }
+  }
   // shifts: pairs (Im > 0) then real poles; c = 2 alpha for pairs, alpha for real poles
   const int s = (int)bestP.upper.size() + (int)bestP.real.size();
   int p = 0;

@@ -129,3 +129,14 @@ def test_late_time_weights_match_the_oracle_and_help_late_channels(lib):
     assert e_w[-1] < 1e-2 * e_u[-1]
     assert e_w[0] > e_u[0]
     assert np.max(w * e_w) <= 1.01 * err
+
+
+@pytest.mark.parametrize("lo,hi,K,m", [(-4, -3.5, 5, 30), (-4, -3.5, 5, 64), (-5, -3, 21, 48), (-5, -2, 31, 64)])
+def test_saturated_fits_keep_poles_off_the_spectrum(lib, lo, hi, K, m):
+    """Degrees far past the error floor: every shift stays off [0, inf) (the spurious real
+    doublets a saturated fit can leave there are dropped) and the uniform error stays at
+    rounding level."""
+    t = np.logspace(lo, hi, K)
+    sh, c, err = lib.poles_residues(t, m)
+    assert np.all((sh.real < 0) | (sh.imag != 0))
+    assert np.all(np.isfinite(c)) and err < 1e-10
