@@ -9,11 +9,14 @@ bracketed by a barrier and a device synchronisation, timed with CUDA events on t
 stream; the working set (10 shifts x 6.4M edges, ~5.7 GB) is far larger than L2.
 
 Extra keys: the FP64 path's models/s on the same model and its per-channel agreement with the
-mixed path, per-step p50/p99, an end-to-end number through the C ABI from host buffers,
-the roofline of the dominant kernel, the CPU oracle timed on a bounded sample, and the SM
-clocks sampled during the timed region.
+mixed path, per-step p50/p99, an end-to-end number through the C ABI from host buffers, the
+roofline of the stencil pass (and of the update pass and the whole iteration), the derivative
+actions on the 96^3 adjoint model, a continuous-batching sample of the serving stream, the CPU
+oracle timed on a bounded sample with one process per shift, and the SM clocks sampled during
+the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --serving-only --serve-requests 256     (the whole serving stream, one line)
 Under torchrun each rank runs its own models (independent problems, no collective on the
 data path); value = all ranks' models / the slowest rank's time.
 """
@@ -37,16 +40,28 @@ WORKLOADS = {"randblock128": 128, "randblock96": 96, "randblock64": 64}
 METRIC = "TEM forward models/s at 128^3 (mixed precision, FP64 residual 1e-12)"
 UNIT = "models/s"
 HBM_FALLBACK_GBS = 6800.0
-# algorithmic bytes per interior edge per shift of one launch, FP32 sweeps with the nodal
-# preconditioner (complex FP32 = 8 B; a nodal vector is 1/3 of an edge vector: 8/3 B per edge):
-NODE = 8.0 / 3.0
-PASS_BYTES = {
-    # read w, a_old, M_e, psi, b_old; write a, q, b, G^T M p
-    "stencil": 16.0 + 16.0 + 4.0 + 4 * NODE,
-    # read x, w, a, q, M_e, diag K; x_n, b, u, G^T M p, cn, W_n; write x, w; x_n, u, psi
-    "update": 32.0 + 16.0 + 8.0 + 8 * NODE + 0.5 * NODE,
-}
-KERNEL_NAMES = {"stencil": "k_cocg_stencil_pipe", "update": "k_cocg_update<float>"}
+NODE = 8.0 / 3.0      # bytes per edge of one complex FP32 nodal vector (one entry per node)
+
+
+def pass_bytes(s):
+    """Bytes per interior edge per shift of one launch of each FP32 pass.
+
+    "survey": the minimal two-pass COCG count -- the stencil reads r, p_old and writes p, q
+    (32 B), the update reads x, r, p, q and writes x, r (48 B) -- plus the M_e plane, 4 B per
+    edge per pass, amortised over the s shifts that sweep a tile together.
+    "kernel": what the kernels move (ncu-verified): the same edge vectors plus the nodal
+    vectors of the preconditioner, and the per-grid arrays (packed masses, diag K, M_e, W_n)
+    read once per tile for all s shifts."""
+    return {
+        "survey": {"stencil": 32.0 + 4.0 / s, "update": 48.0 + 4.0 / s},
+        "kernel": {
+            # edges w, a_old read, a, q written; nodes psi, b_old read, b, G^T M p written; masses
+            "stencil": 32.0 + 4 * NODE + (16.0 / 3.0) / s,
+            # edges x, a, w, q read, x, w written; diag K, M_e; nodes x_n, b, u, G^T M p, c_n read,
+            # x_n, u, psi written; W_n
+            "update": 48.0 + 8.0 / s + 8 * NODE + (4.0 / 3.0) / s,
+        },
+    }
 
 
 def _dist():
@@ -133,13 +148,13 @@ def _config(workload, nside, model, n_shifts):
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "solver.cu"):
+    for f in ("kernels.cuh", "stencil_tma.cuh", "solver.cu"):
         with open(os.path.join(ROOT, "paper_2506_11657_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel, units):
+def _traffic(which, units):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on today's kernels."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
@@ -147,114 +162,162 @@ def _traffic(kernel, units):
             t = json.load(f)
         if t.get("source_sha") != _kernel_sha():
             return None
-        per_unit = t["kernels"][kernel]["dram_bytes_per_unit"]
-        return float(per_unit * units)
+        return float(t["kernels"][which]["dram_bytes_per_unit"] * units)
     except Exception:
         return None
 
 
-def cpu_oracle_sample(model, shifts, iters_per_shift, n_iter=12):
-    """Time the CPU oracle on a bounded sample of the same model: assembly once, then n_iter
-    Jacobi-COCG iterations of the first shift; scale to a whole model with the per-shift
-    iteration counts (sum over shifts) of the solve.  Returns (models/s, seconds, description)."""
-    from oracle.tem import TEMProblem
-    from oracle.solvers import solve_cocg
+# ------------------------------------------------------------------ CPU oracle legs
+def oracle_sample(name, steps, warmup, m):
+    """The oracle's iterative route (T2) on every shift of `name`, the shifts spread over
+    min(cores, s) processes (the paper's one process per pole).  A step runs, in every process,
+    T2 capped at m iterations for each of its shifts; step(0) gives the solver's set-up alone.
+    The whole-model time is assembly + set-up + the oracle's own per-shift iteration counts
+    (oracle/t2_counts_<name>.json, written by `python -m oracle.t2_counts <name>`) scheduled
+    over the processes at the measured time per iteration.  Returns a dict, or None without
+    the stored counts."""
+    from oracle import rational as R
+    from oracle import t2_counts as T
+    from paper_2506_11657_gb300 import workloads as W
+    rec = T.load_counts(name)
+    if rec is None:
+        return None
+    model = W.randblock128(n=WORKLOADS[name])
+    shifts, _, _ = R.tem_poles_residues(model.t, model.degree)
+    S = T.Sampler(name, shifts)
+    try:
+        setup = S.step(0)
+        for _ in range(warmup):
+            S.step(m)
+        times = [S.step(m) for _ in range(steps)]
+        model_s = S.model_seconds(setup, float(np.median(times)), m, rec["iterations"])
+        return {"model_s": model_s, "step_s": times, "setup_s": setup, "assembly_s": S.assembly_s,
+                "processes": S.processes, "cores_available": S.cores_available, "iterations": rec["iterations"],
+                "m": m}
+    finally:
+        S.close()
+
+
+def cpu_baseline_leg():
+    """The CPU baseline of the GPU arm: the 128^3 sample (scaled to a whole model by the oracle's
+    own iteration counts) and one whole 32^3 model of the same family solved end to end."""
+    from oracle import t2_counts as T
+    smp = oracle_sample("randblock128", steps=1, warmup=0, m=3)
+    if smp is None:
+        return None
+    whole = T.count("randblock32")
+    desc = (f"oracle T2 (Jacobi-COCG, FP64) on randblock128: {smp['processes']} processes, one per shift; "
+            f"assembly {smp['assembly_s']:.1f} s, solver set-up {smp['setup_s']:.1f} s, then {smp['m']} "
+            f"iterations of every shift ({smp['step_s'][0]:.2f} s); whole model = assembly + set-up + the "
+            f"oracle's own T2 counts per shift (max {max(smp['iterations'])}, counted once by oracle.t2_counts) "
+            f"at the measured time per iteration")
+    return {"value": 1.0 / smp["model_s"], "unit": UNIT, "cores": smp["processes"],
+            "cores_available": smp["cores_available"], "kind": "oracle", "sample": desc,
+            "model_s_estimate": smp["model_s"],
+            "whole_model_measured": {"workload": "randblock32 (32^3 cells, same recipe)", "processes": whole["processes"],
+                                     "seconds": whole["wall_s"], "iterations": whole["iterations"]}}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, as it stands, on the same workload and metric.  Each
+    step is a bounded sample (3 T2 iterations of every shift, one process per shift)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2506_11657_gb300 import workloads as W
+    model = W.randblock128()
     t0 = time.perf_counter()
-    P = TEMProblem(model.hx, model.hy, model.hz, model.sigma, model.loop_xy, model.z_loop, model.rx,
-                   origin=model.origin)
-    t1 = time.perf_counter()
-    solve_cocg(P.K, P.Md, P.f, shifts[0], tol=1e-300, maxiter=n_iter)
-    t2 = time.perf_counter()
-    per_iter = (t2 - t1) / n_iter
-    total_iters = float(np.sum(iters_per_shift))
-    model_s = (t1 - t0) + per_iter * total_iters
-    desc = (f"oracle.TEMProblem assembly ({t1 - t0:.1f} s) + {n_iter} Jacobi-COCG iterations of one shift "
-            f"({per_iter:.3f} s each, single process), scaled to a whole model by {int(total_iters)} iterations: "
-            f"the FP64 Jacobi-COCG count of the {len(shifts)} shifts to 1e-12, counted once on the GPU FP64 "
-            f"Jacobi path (the same recurrence; counting it with the oracle would take hours)")
-    return 1.0 / model_s, t2 - t0, desc
+    smp = oracle_sample("randblock128", steps=args.steps, warmup=args.warmup, m=3)
+    wall = time.perf_counter() - t0
+    if smp is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle/t2_counts_randblock128.json is missing"}))
+        return
+    value = 1.0 / smp["model_s"]
+    desc = (f"each step: 3 iterations of oracle T2 (Jacobi-COCG, FP64) on every shift of randblock128, "
+            f"{smp['processes']} processes (one per shift); value = 1 / (assembly {smp['assembly_s']:.1f} s + "
+            f"set-up {smp['setup_s']:.1f} s + the oracle's own T2 counts per shift at the measured time "
+            f"per iteration)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(smp["step_s"])),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": DATA, "config": _config("randblock128", 128, model, len(smp["iterations"])),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": smp["processes"],
+                             "cores_available": smp["cores_available"], "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
 
 
-def run_serving_sample(n_req, stream):
+# ------------------------------------------------------------------ serving
+def run_serving(n_req, stream):
     """Continuous batching on the first n_req requests of the seeded serving stream (grids of
-    32^3..96^3, 16-20 poles): all arriving at once (capacity), then Poisson arrivals at 1.2x that
-    capacity (latency).  Beside it, the same requests one at a time through tem_forward in FP64."""
+    32^3..96^3, 16-20 poles): all arriving at once (capacity), then Poisson arrivals at 1.2x and
+    0.5x that capacity (latency).  Beside it, the same requests one at a time through tem_forward
+    in FP64 (the plain per-model GPU path)."""
     import torch
     from paper_2506_11657_gb300 import tem, workloads as W
     from paper_2506_11657_gb300.serving import PoleCache, run_stream
-    stream_items = W.serving_stream(n_requests=n_req, seed=4)
-    models = [m for _, m in stream_items]
+    models = [m for _, m in W.serving_stream(n_requests=n_req, seed=4)]
     poles = PoleCache()
     for m in models:
         poles.get(m.t, m.degree)
     torch.cuda.synchronize()
     srv = tem.Server(stream=stream)
     _, sat = run_stream(srv, [(0.0, m) for m in models], poles)
-    cap = sat["models_per_s"]
-    rng = np.random.default_rng(4)
-    arr = np.cumsum(rng.exponential(1.0 / (1.2 * cap), size=len(models)))
-    srv2 = tem.Server(stream=stream)
-    _, lat = run_stream(srv2, [(float(a), m) for a, m in zip(arr, models)], poles)
     srv.close()
-    srv2.close()
-    # the served mixed form against FP64 one model at a time, on the same quarter of the requests
-    k = max(1, len(models) // 4)
-    srv3 = tem.Server(stream=stream)
-    _, sat_k = run_stream(srv3, [(0.0, m) for m in models[:k]], poles)
-    srv3.close()
+    cap = sat["models_per_s"]
+    out = {"workload": "serving_stream", "requests": len(models), "grids": sorted(set(len(m.hx) for m in models)),
+           "capacity_models_per_s": cap, "failed": sat["failed"]}
+    for load in (1.2, 0.5):
+        rng = np.random.default_rng(4)
+        arr = np.cumsum(rng.exponential(1.0 / (load * cap), size=len(models)))
+        s2 = tem.Server(stream=stream)
+        _, lat = run_stream(s2, [(float(a), m) for a, m in zip(arr, models)], poles)
+        s2.close()
+        out[f"load_{load}x"] = {"arrival_rate_per_s": load * cap, "models_per_s": lat["models_per_s"],
+                                "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
+                                "mean_queue_ms": lat["mean_queue_ms"], "failed": lat["failed"]}
     t0 = time.perf_counter()
-    for m in models[:k]:
+    for m in models:
         g = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma, stream=stream)
         sh, c = poles.get(m.t, m.degree)
         tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, tem.default_options(precision="fp64"), stream=stream)
         g.close()
     torch.cuda.synchronize()
-    fp64_rate = k / (time.perf_counter() - t0)
-    sizes = sorted(set(len(m.hx) for m in models))
-    return {"workload": "serving_stream", "requests": len(models), "grids": sizes,
-            "capacity_models_per_s": cap, "arrival_rate_per_s": 1.2 * cap,
-            "models_per_s": lat["models_per_s"], "p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"],
-            "mean_queue_ms": lat["mean_queue_ms"], "failed": sat["failed"] + lat["failed"],
-            "sample_requests": k, "served_mixed_sample_models_per_s": sat_k["models_per_s"],
-            "fp64_one_at_a_time_sample_models_per_s": fp64_rate}
+    out["fp64_one_at_a_time_models_per_s"] = len(models) / (time.perf_counter() - t0)
+    out["served_over_fp64"] = cap / out["fp64_one_at_a_time_models_per_s"]
+    return out
 
 
-def run_reference(args):
-    """--impl reference: the CPU oracle, as it stands, on the same workload and metric."""
-    ws, rank, _ = _dist()
-    if rank != 0:
-        return
-    from paper_2506_11657_gb300 import workloads as W
-    from oracle import rational as R
-    model = W.randblock128()
-    shifts, c, err = R.tem_poles_residues(model.t, model.degree)
-    # iteration counts per shift of FP64 Jacobi-COCG to 1e-12 on this model (recorded from the
-    # GPU FP64 path; the oracle's T2 iterates the same recurrences)
-    iters = ORACLE_ITERS_128
-    vals = []
-    t_start = time.perf_counter()
-    for step in range(args.warmup + args.steps):
-        v, secs, desc = cpu_oracle_sample(model, shifts, iters, n_iter=4)
-        if step >= args.warmup:
-            vals.append(v)
-    wall = time.perf_counter() - t_start
-    value = float(np.median(vals))
-    cores = 1
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": DATA, "config": _config("randblock128", 128, model, len(shifts)),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": wall}
-    print(json.dumps(line), flush=True)
-
-
-# Jacobi-COCG iterations per shift to an FP64 relative residual of 1e-12 on randblock128 (the
-# recurrence the oracle's T2 route iterates), counted once on the GPU FP64 Jacobi path because
-# the oracle itself would need hours at this size.  Used only to scale the timed CPU sample to a
-# whole model; no parity check or expected value depends on them.
-ORACLE_ITERS_128 = [5447, 6167, 5111, 3902, 3241, 2971, 3003, 3239, 3991, 6154]
+# ------------------------------------------------------------------ derivatives
+def run_derivatives(stream, dev):
+    """The derivative actions of Sec. 4 on the 96^3 adjoint model (64 receivers, 20 poles, 31
+    channels): J dm (tem_jvp) and J^T g (tem_adjoint), one batched solve each after a forward that
+    keeps its solutions, timed with CUDA events, and the transpose gap <g, J dm> - <J^T g, dm>."""
+    import torch
+    from paper_2506_11657_gb300 import tem, workloads as W
+    m = W.adjoint96()
+    sh, c, _ = tem.poles_residues(m.t, m.degree)
+    g = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma, stream=stream)
+    opt = tem.default_options(precision="mixed", tol=1e-12)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(stream)
+    rk = tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, opt, stream=stream, keep_state=True)
+    e[1].record(stream)
+    rng = np.random.default_rng(7)
+    dm = rng.standard_normal(m.sigma.size) * (m.sigma.ravel() > 1e-6)
+    gres = rng.standard_normal(rk.d.shape)
+    jd = rk.state.jvp(dm, stream=stream)
+    e[2].record(stream)
+    gr = rk.state.adjoint(gres, stream=stream)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    rk.state.close()
+    g.close()
+    lhs, rhs = float(np.sum(gres * jd)), float(np.dot(gr, dm))
+    return {"workload": "adjoint96", "receivers": int(len(m.rx)), "forward_ms": e[0].elapsed_time(e[1]),
+            "jvp_ms": e[1].elapsed_time(e[2]), "adjoint_ms": e[2].elapsed_time(e[3]),
+            "transpose_rel_gap": abs(lhs - rhs) / (np.sum(np.abs(gres * jd)) + np.sum(np.abs(gr * dm)))}
 
 
 def main():
@@ -268,6 +331,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="randblock128", choices=sorted(WORKLOADS))
     ap.add_argument("--serve-requests", type=int, default=16)
+    ap.add_argument("--serving-only", action="store_true")
     ap.add_argument("--no-derivatives", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -288,11 +352,15 @@ def main():
     if not os.path.exists(tem.LIB_PATH):
         B.build()
     tem.lib()
+    stream = torch.cuda.current_stream(dev)
+    if args.serving_only:
+        if rank == 0:
+            print(json.dumps({"serving": run_serving(args.serve_requests, stream)}), flush=True)
+        return
 
     nside = WORKLOADS[args.workload]
     model = W.randblock128(n=nside)
     shifts, c, uerr = tem.poles_residues(model.t, model.degree)
-    stream = torch.cuda.current_stream(dev)
     grid = tem.Grid(model.hx, model.hy, model.hz, model.origin, model.sigma, stream=stream)
     opt_mixed = tem.default_options(precision="mixed", tol=1e-12)
     opt_fp64 = tem.default_options(precision="fp64", tol=1e-12)
@@ -333,7 +401,7 @@ def main():
         total_ms = float(t.item())
     value = ws * args.steps / (total_ms / 1000.0)
 
-    # FP64 path on the same model, and agreement of the two (cancellation-aware floor)
+    # FP64 path on the same model, and the per-channel agreement of the two
     fp64 = None
     if args.fp64_steps > 0:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -353,21 +421,10 @@ def main():
                 "median_rel_err_mixed_vs_fp64": float(np.median(rel)),
                 "channels_rel_le_1e-5": int((rel <= 1e-5).sum()), "channels": int(rel.size)}
 
-    # the derivative actions of Sec. 4 on the same model: J dm (tem_jvp) and J^T g (tem_adjoint),
-    # one batched solve each, timed with CUDA events after a forward that keeps its solutions
-    derivs = None
+    # all K field snapshots of the 128^3 model (the columns of S R): s complex FP64 read, K FP64 written per edge
+    snaps = None
     if not args.no_derivatives:
         rk = fwd(opt_mixed, keep=True)
-        rng = np.random.default_rng(7)
-        dm = rng.standard_normal(model.sigma.size) * (model.sigma.ravel() > 1e-6)
-        g = rng.standard_normal(rk.d.shape)
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        e0.record(stream)
-        jd = rk.state.jvp(dm, stream=stream)
-        e1.record(stream)
-        gr = rk.state.adjoint(g, stream=stream)
-        e2.record(stream)
-        # all K field snapshots (the columns of S R): reads s complex FP64 and writes K FP64 per edge
         U = torch.empty((len(model.t), 3 * model.sigma.size), dtype=torch.float64, device=dev)
         rk.state.fields(out=U, stream=stream)
         e3, e4 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -377,28 +434,46 @@ def main():
         torch.cuda.synchronize()
         rk.state.close()
         del U
-        fields_ms = e3.elapsed_time(e4)
-        fields_bytes = 3 * model.sigma.size * (16 * len(shifts) + 8 * len(model.t))
-        lhs, rhs = float(np.sum(g * jd)), float(np.dot(gr, dm))
-        derivs = {"jvp_ms": e0.elapsed_time(e1), "adjoint_ms": e1.elapsed_time(e2),
-                  "forward_ms": float(np.median(step_ms)),
-                  "transpose_rel_gap": abs(lhs - rhs) / (np.sum(np.abs(g * jd)) + np.sum(np.abs(gr * dm))),
-                  "fields_ms_all_channels": fields_ms, "fields_gbs": fields_bytes / (fields_ms * 1e-3) / 1e9}
+        fms = e3.elapsed_time(e4)
+        fbytes = 3 * model.sigma.size * (16 * len(shifts) + 8 * len(model.t))
+        snaps = {"ms_all_channels": fms, "gbs": fbytes / (fms * 1e-3) / 1e9}
+    derivs = run_derivatives(stream, dev) if not args.no_derivatives else None
 
-    # per-kernel timing of the passes (dominant kernel roofline)
+    # per-launch timing of the passes with all shifts active (CUDA events on the launching stream)
     prof = tem.profile_passes(grid, model.loop_xy, model.z_loop, shifts, tem.PREC_MIXED, n_iter=20, stream=stream)
     peak, peak_kind = _peaks()
     units = prof["units"]
-    gbs = {k: PASS_BYTES[k] * units / (prof[k + "_ms"] * 1e-3) / 1e9 for k in PASS_BYTES}
-    dom = max(PASS_BYTES, key=lambda k: prof[k + "_ms"])
-    it_ms = sum(prof[k + "_ms"] for k in PASS_BYTES)
-    roofline = {"bound": "hbm", "achieved": gbs[dom], "peak": peak, "unit": "GB/s", "frac": gbs[dom] / peak,
-                "traffic": _traffic(dom, units), "kernel": KERNEL_NAMES[dom], "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": PASS_BYTES[dom] * units, "units_per_launch": units,
-                "iteration_gbs": sum(PASS_BYTES.values()) * units / (it_ms * 1e-3) / 1e9,
-                "iteration_frac": sum(PASS_BYTES.values()) * units / (it_ms * 1e-3) / 1e9 / peak,
-                "pass_ms": {k: prof[k + "_ms"] for k in ("stencil", "update", "residual")},
-                "pass_gbs": gbs}
+    s = len(shifts)
+    pb = pass_bytes(s)
+    tma = os.environ.get("TEM_FP32_STENCIL", "") != "pipe" and nside % 2 == 0
+
+    def gbs(nbytes, ms):
+        return nbytes * units / (ms * 1e-3) / 1e9
+
+    def leg(which, ms):
+        a = gbs(pb["survey"][which], ms)
+        k = gbs(pb["kernel"][which], ms)
+        return {"launch_ms": ms, "achieved": a, "frac": a / peak, "bytes_per_unit": pb["survey"][which],
+                "kernel_bytes": {"bytes_per_unit": pb["kernel"][which], "achieved": k, "frac": k / peak},
+                "traffic": _traffic(which, units)}
+
+    st = leg("stencil", prof["stencil_ms"])
+    up = leg("update", prof["update_ms"])
+    it_ms = prof["stencil_ms"] + prof["update_ms"]
+    it_survey = (pb["survey"]["stencil"] + pb["survey"]["update"])
+    it_kernel = (pb["kernel"]["stencil"] + pb["kernel"]["update"])
+    roofline = {"bound": "hbm", "kernel": "k_cocg_stencil_tma" if tma else "k_cocg_stencil_pipe",
+                "achieved": st["achieved"], "peak": peak, "unit": "GB/s", "frac": st["frac"],
+                "traffic": st["traffic"], "peak_source": peak_kind,
+                "bytes_per_unit": st["bytes_per_unit"], "units_per_launch": units,
+                "algorithmic_bytes_per_launch": st["bytes_per_unit"] * units, "launch_ms": st["launch_ms"],
+                "kernel_bytes": st["kernel_bytes"], "stencil_ctas_per_sm": prof["stencil_ctas_per_sm"],
+                "update": dict(up, kernel="k_cocg_update_vec" if tma else "k_cocg_update<float>"),
+                "iteration": {"ms": it_ms, "achieved": gbs(it_survey, it_ms), "frac": gbs(it_survey, it_ms) / peak,
+                              "kernel_bytes": {"achieved": gbs(it_kernel, it_ms), "frac": gbs(it_kernel, it_ms) / peak}},
+                "residual_ms": prof["residual_ms"],
+                "byte_counts": "achieved/frac: survey bytes (two-pass COCG vectors + M_e/s); kernel_bytes: what the "
+                               "kernels move incl. the nodal preconditioner (ncu-verified)"}
 
     # end to end through the C ABI from host buffers: grid upload + forward + result read-back
     e2e_steps = args.e2e_steps
@@ -415,12 +490,12 @@ def main():
     e2e = {"value": e2e_steps / (time.perf_counter() - t0) if e2e_steps else None, "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
-    serving = run_serving_sample(args.serve_requests, stream) if args.serve_requests > 0 else None
+    serving = run_serving(args.serve_requests, stream) if args.serve_requests > 0 else None
+    grid.close()
 
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline and nside == 128:   # the iteration counts are for 128^3
-        v, secs, desc = cpu_oracle_sample(model, shifts, ORACLE_ITERS_128)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc, "seconds": secs}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and nside == 128:
+        cpu = cpu_baseline_leg()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -432,7 +507,7 @@ def main():
                 "iters_per_shift_mixed": iters_mixed.tolist(), "relres_mixed": relres_mixed.tolist(),
                 "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(n1 - n0), "clocks": clocks, "serving": serving,
-                "derivatives": derivs}
+                "derivatives": derivs, "field_snapshots": snaps}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -73,16 +73,17 @@ typedef struct tem_options {
   int32_t precision;     /* TEM_PREC_FP64 (default) or TEM_PREC_MIXED */
   int32_t max_iter;      /* bound on COCG iterations per shift (default 20000) */
   double tol;            /* stop when ||f - A_i x_i||_2 <= tol ||f||_2, FP64 residual (default 1e-12) */
-  double inner_tol;      /* MIXED: relative residual reduction per FP32 inner solve (default 1e-3) */
+  double inner_tol;      /* MIXED: relative residual reduction per FP32 inner solve (default 1e-1) */
   int32_t max_outer;     /* MIXED: bound on FP64 defect-correction steps (default 40) */
   int32_t check_every;   /* iterations between host-side convergence polls (default 32) */
   int32_t keep_state;    /* nonzero: keep the solutions for tem_adjoint (state_out must be non-NULL) */
   int32_t precond;       /* TEM_PRECOND_AUTO (default), TEM_PRECOND_JACOBI or TEM_PRECOND_NODAL */
-  int32_t carry_direction; /* MIXED: 0 (default): every inner solve restarts from the true
-                            residual (plain defect correction); nonzero: an FP64 outer step
-                            replaces the inner residual by the true one and the inner COCG
-                            keeps its search direction (residual replacement).  A solve that
-                            follows a stagnated inner solve restarts either way */
+  int32_t carry_direction; /* MIXED: nonzero (default 1): an FP64 outer step replaces the inner
+                            residual by the true one and the inner COCG keeps its search
+                            direction (residual replacement, once per inner_tol reduction);
+                            0: every inner solve restarts from the true residual (plain defect
+                            correction).  A solve that follows a stagnated inner solve restarts
+                            either way */
 } tem_options;
 
 /* Preconditioner of the inner COCG sweeps. */

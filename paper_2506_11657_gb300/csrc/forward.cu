@@ -574,7 +574,7 @@ int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_ve
   }
   ms_out[0] = tot_s / n_iter;
   ms_out[1] = tot_u / n_iter;
-  ms_out[3] = precision == TEM_PREC_MIXED ? stencil_pipe_occupancy() : 0;
+  ms_out[3] = precision == TEM_PREC_MIXED ? stencil_f32_occupancy(b.uses_tma()) : 0;
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   if (units_out) {

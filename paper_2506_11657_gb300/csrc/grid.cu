@@ -146,6 +146,13 @@ __global__ void k_diagK(int nx, int ny, int nz, const double* L, const double* S
   }
 }
 
+// (M_x, M_y, M_z, W_n) per node in one FP32 record: the tile loads of the FP32 stencil pass
+// fetch the masses a node's edges need as one 16-byte element.
+__global__ void k_pack_mass(int64_t ncomp, const float* Mef, const float* Wnf, float4* Mq) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < ncomp; n += (int64_t)gridDim.x * blockDim.x)
+    Mq[n] = make_float4(Mef[n], Mef[ncomp + n], Mef[2 * ncomp + n], Wnf[n]);
+}
+
 static bool finite_positive(const double* a, int64_t n) {
   for (int64_t q = 0; q < n; ++q)
     if (!(std::isfinite(a[q]) && a[q] > 0.0)) return false;
@@ -193,6 +200,10 @@ static int upload_sigma(tem_grid* g, const double* sigma, cudaStream_t st) {
       nx, ny, nz, geo, geo + nx, geo + nx + ny, Me, Wn, Wnf);
   count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
+  k_pack_mass<<<(int)std::min<int64_t>((ncell + threads - 1) / threads, 152 * 32), threads, 0, st>>>(
+      ncell, Mef, Wnf, g->mq.as<float4>());
+  count_launch();
+  TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
 }
 
@@ -230,11 +241,11 @@ void tem_default_options(tem_options* opt) {
   opt->precision = TEM_PREC_FP64;
   opt->max_iter = 20000;
   opt->tol = 1e-12;
-  opt->inner_tol = 1e-3;
+  opt->inner_tol = 1e-1;
   opt->max_outer = 40;
   opt->check_every = 32;
   opt->keep_state = 0;
-  opt->carry_direction = 0;
+  opt->carry_direction = 1;
 }
 
 int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, const double* hz, int64_t nz,
@@ -276,6 +287,7 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   int rc = g->geo.alloc(9 * n1 * (sizeof(double) + sizeof(float)), st);
   if (rc == TEM_OK) rc = g->me.alloc(7 * ncell * (sizeof(double) + sizeof(float)), st);
   if (rc == TEM_OK) rc = g->sig.alloc(ncell * sizeof(double), st);
+  if (rc == TEM_OK) rc = g->mq.alloc(ncell * sizeof(float4), st);
   if (rc != TEM_OK) {
     delete g;
     return rc;
@@ -305,6 +317,7 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny, c
   v.Mef = reinterpret_cast<const float*>(v.dK + 3 * ncell);
   v.Wnf = v.Mef + 3 * ncell;
   v.dKf = v.Wnf + ncell;
+  v.Mq = g->mq.as<float4>();
   {
     double* dK = const_cast<double*>(v.dK);
     float* dKf = const_cast<float*>(v.dKf);

@@ -21,6 +21,8 @@
 // the faces of plane k-1 that an edge needs stay in registers.
 #pragma once
 
+#include <cuda.h>
+
 #include "tem_internal.h"
 
 namespace tem {
@@ -331,12 +333,18 @@ __device__ __forceinline__ void stencil_march(StencilSmem<T>& sm, const GridView
 }
 
 // --------------------------------------------------------------- slot plumbing
+// Block lists: CTA -> (slot, the CTA's block index within the slot).  The lists interleave the
+// slots block by block (see build_block_maps), and a slot's arithmetic depends only on its own
+// block index, never on its position in the list.  In FP32, the stencil and update lists hold
+// first the blocks of the slots that take the TMA / 16-byte kernels (even nx), then the others;
+// each part is its own launch, so a slot runs the same kernels whatever else is in the batch.
 struct BatchArgs {
   const SlotDesc* slots;
   SlotScalars* sc;
-  const int* blk2slot;       // stencil / residual launch: CTA -> slot
-  const int* ublk2slot;      // update launch: CTA -> slot
-  const int* nblk2slot;      // nodal launch: CTA -> slot
+  const int2* blk2slot;      // stencil / residual launch
+  const int2* ublk2slot;     // update launch
+  const int2* nblk2slot;     // nodal launch
+  const CUtensorMap* tmaps;  // [slot][7] tile maps of the FP32 stencil pass (or NULL)
   double* part;              // [slot][part_stride] partial sums
   unsigned* ticket;          // [slot]
   int* n_active;             // slots armed or iterating
@@ -502,11 +510,11 @@ struct CocgStencilPol {
 template <class T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) k_cocg_stencil(BatchArgs A) {
   __shared__ StencilSmem<T> sm;
-  const int slot = A.blk2slot[blockIdx.x];
+  const int2 bm = A.blk2slot[blockIdx.x];
+  const int slot = bm.x, lb = bm.y;
   SlotScalars* S = A.sc + slot;
   if (!S->active) return;
   const SlotDesc& d = A.slots[slot];
-  const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
   tile_of(d, lb, d.g.nz, i0, j0, k0, k1);
   CocgStencilPol<T> pol(d.g);
@@ -693,12 +701,12 @@ __device__ __forceinline__ void pipe_faces(pipe::Smem& sm, int bk, int bk1, floa
 static __global__ void __launch_bounds__(NT, TEM_PIPE_MIN_CTAS) k_cocg_stencil_pipe(BatchArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pipe::Smem& sm = *reinterpret_cast<pipe::Smem*>(smem_raw);
-  const int slot = A.blk2slot[blockIdx.x];
+  const int2 bm = A.blk2slot[blockIdx.x];
+  const int slot = bm.x, lb = bm.y;
   SlotScalars* S = A.sc + slot;
   if (!S->active) return;
   const SlotDesc& d = A.slots[slot];
   const GridView& g = d.g;
-  const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
   tile_of(d, lb, g.nz, i0, j0, k0, k1);
   PipeArgs pa;
@@ -964,12 +972,12 @@ __device__ __forceinline__ void start_direction(SlotScalars* S, double rho_re, d
 template <class T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(BatchArgs A) {
   __shared__ double red[NT / 32 * 4];
-  const int slot = A.ublk2slot[blockIdx.x];
+  const int2 bm = A.ublk2slot[blockIdx.x];
+  const int slot = bm.x, lb = bm.y;
   SlotScalars* S = A.sc + slot;
   if (!S->active) return;
   const SlotDesc& d = A.slots[slot];
   const GridView& g = d.g;
-  const int lb = blockIdx.x - d.blk_update0;
   const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
   const C2<T> xi(T(d.xi_re), T(d.xi_im));
   const bool first = S->iters == 0;                 // the correction starts at 0
@@ -1054,6 +1062,141 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
   }
 }
 
+// ---------- pass B in FP32, two entries per access (16-byte loads and stores)
+// The arithmetic of k_cocg_update<float> on entry pairs (2e, 2e+1) of the slot's flat stream:
+// 3 n/2 edge pairs, then n/2 node pairs (n = nx ny nz, even for the slots that use this kernel).
+// Each thread keeps U pairs of every input in flight before it computes.
+__device__ __forceinline__ void update_edge(float& x_re, float& x_im, float& w_re, float& w_im, float a_re, float a_im,
+                                            float q_re, float q_im, float dk, float me, C2<float> alpha, float xr,
+                                            float xim, C2<float>& rz, float& rr) {
+  if (dk == 0.f) return;   // boundary entry: x and w stay as they are (0)
+  x_re += alpha.re * a_re - alpha.im * a_im;
+  x_im += alpha.re * a_im + alpha.im * a_re;
+  const C2<float> D(dk - me * xr, -me * xim);
+  const C2<float> r = cmul(D, C2<float>(w_re, w_im)) - cmul(alpha, C2<float>(q_re, q_im));
+  const C2<float> wn = cdiv(r, D);
+  w_re = wn.re;
+  w_im = wn.im;
+  rz = rz + cmul(r, wn);
+  rr += r.re * r.re + r.im * r.im;
+}
+
+__device__ __forceinline__ void update_node(float& xn_re, float& xn_im, float& u_re, float& u_im, float& ps_re,
+                                            float& ps_im, float b_re, float b_im, float gp_re, float gp_im, float cn_re,
+                                            float cn_im, float wn, C2<float> alpha, C2<float> xi, C2<float>& rn) {
+  xn_re += alpha.re * b_re - alpha.im * b_im;
+  xn_im += alpha.re * b_im + alpha.im * b_re;
+  if (wn == 0.f) return;   // boundary node: u and psi stay 0
+  u_re += alpha.re * gp_re - alpha.im * gp_im;
+  u_im += alpha.re * gp_im + alpha.im * gp_re;
+  const C2<float> dv = C2<float>(cn_re, cn_im) + cmul(xi, C2<float>(u_re, u_im));
+  const C2<float> ps = cdiv(dv, wn * C2<float>(-xi.re, -xi.im));
+  ps_re = ps.re;
+  ps_im = ps.im;
+  rn = rn + cmul(dv, ps);
+}
+
+static __global__ void __launch_bounds__(NT, 3) k_cocg_update_vec(BatchArgs A) {
+  __shared__ double red[NT / 32 * 4];
+  const int2 bm = A.ublk2slot[blockIdx.x];
+  const int slot = bm.x, lb = bm.y;
+  SlotScalars* S = A.sc + slot;
+  if (!S->active) return;
+  const SlotDesc& d = A.slots[slot];
+  const int64_t nc = d.g.ncomp;
+  const C2<float> alpha(float(S->alpha_re), float(S->alpha_im));
+  const C2<float> xi(float(d.xi_re), float(d.xi_im));
+  const bool first = S->iters == 0;                 // the correction starts at 0
+  const float4* __restrict__ av = static_cast<const float4*>(S->parity ? d.a0 : d.a1);
+  const float4* __restrict__ bv = static_cast<const float4*>(S->parity ? d.b0 : d.b1);
+  const float4* __restrict__ qv = static_cast<const float4*>(d.q);
+  float4* __restrict__ wv = static_cast<float4*>(d.w);
+  float4* __restrict__ xv = static_cast<float4*>(d.x);
+  const float2* __restrict__ dK = reinterpret_cast<const float2*>(d.g.dKf);
+  const float2* __restrict__ Me = reinterpret_cast<const float2*>(d.g.Mef);
+  const float2* __restrict__ Wn = reinterpret_cast<const float2*>(d.g.Wnf);
+  const int64_t ne2 = 3 * nc / 2, n2 = ne2 + (d.nodal ? nc / 2 : 0);
+  const int64_t per = (n2 + d.nblk_update - 1) / d.nblk_update;
+  const int64_t p0 = (int64_t)lb * per, p1 = min(n2, p0 + per);
+  C2<float> rz = czero<float>(), rn = czero<float>();
+  float rr = 0.f;
+  constexpr int U = 2;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int64_t pe = min(p1, ne2);
+  for (int64_t base = p0 + threadIdx.x; base < pe; base += (int64_t)NT * U) {
+    float2 dk[U], me[U];
+    float4 ar[U], qr[U], wr[U], xr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + (int64_t)u * NT;
+      if (p < pe) {
+        dk[u] = __ldg(dK + p);
+        me[u] = __ldg(Me + p);
+        ar[u] = __ldg(av + p);
+        qr[u] = __ldg(qv + p);
+        wr[u] = wv[p];
+        xr[u] = first ? z4 : xv[p];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + (int64_t)u * NT;
+      if (p >= pe) continue;
+      update_edge(xr[u].x, xr[u].y, wr[u].x, wr[u].y, ar[u].x, ar[u].y, qr[u].x, qr[u].y, dk[u].x, me[u].x, alpha,
+                  xi.re, xi.im, rz, rr);
+      update_edge(xr[u].z, xr[u].w, wr[u].z, wr[u].w, ar[u].z, ar[u].w, qr[u].z, qr[u].w, dk[u].y, me[u].y, alpha,
+                  xi.re, xi.im, rz, rr);
+      xv[p] = xr[u];
+      wv[p] = wr[u];
+    }
+  }
+  // nodal pairs: x_n += alpha b;  u = G^T M d += alpha G^T M p;  psi = (cn + xi u) / D_n
+  const float4* __restrict__ gpv = static_cast<const float4*>(d.gp);
+  const float4* __restrict__ cnv = static_cast<const float4*>(d.cn);
+  float4* __restrict__ xnv = static_cast<float4*>(d.xn);
+  float4* __restrict__ uv = static_cast<float4*>(d.u);
+  float4* __restrict__ psv = static_cast<float4*>(d.psi);
+  for (int64_t base = max(p0, ne2) + threadIdx.x; base < p1; base += (int64_t)NT * U) {
+    float2 wn[U];
+    float4 br[U], gr[U], cr[U], xr[U], ur[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t m = base + (int64_t)u * NT - ne2;
+      if (m + ne2 < p1) {
+        wn[u] = __ldg(Wn + m);
+        br[u] = __ldg(bv + m);
+        gr[u] = __ldg(gpv + m);
+        cr[u] = __ldg(cnv + m);
+        xr[u] = first ? z4 : xnv[m];
+        ur[u] = first ? z4 : uv[m];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t m = base + (int64_t)u * NT - ne2;
+      if (m + ne2 >= p1) continue;
+      float4 pr = z4;
+      update_node(xr[u].x, xr[u].y, ur[u].x, ur[u].y, pr.x, pr.y, br[u].x, br[u].y, gr[u].x, gr[u].y, cr[u].x,
+                  cr[u].y, wn[u].x, alpha, xi, rn);
+      update_node(xr[u].z, xr[u].w, ur[u].z, ur[u].w, pr.z, pr.w, br[u].z, br[u].w, gr[u].z, gr[u].w, cr[u].z,
+                  cr[u].w, wn[u].y, alpha, xi, rn);
+      xnv[m] = xr[u];
+      uv[m] = ur[u];
+      psv[m] = pr;
+    }
+  }
+  rz = rz + rn;
+  double v[3] = {double(rz.re), double(rz.im), double(rr)};
+  block_sum<3, NT>(v, red);
+  double* part = A.part + (int64_t)slot * A.part_stride;
+  if (publish_partial<3>(v, part, A.ticket + slot, d.nblk_update, lb)) {
+    double tot[3];
+    sum_partials<3, NT>(part, d.nblk_update, tot, red);
+    if (threadIdx.x != 0) return;
+    finish_iteration(S, A.n_active, tot[0], tot[1], tot[2]);
+  }
+}
+
 // ------------------------------ pass C: psi = D_n^{-1} G^T r;  rho = (r, D^-1 r) + (G^T r, psi)
 // G^T r is not formed from r: in the air D_n is tiny, and rounding in the divergence of r
 // would be amplified by 1/D_n.  Instead, with G^T K = 0 (curl grad = 0) and G^T b_outer = 0
@@ -1111,7 +1254,8 @@ __device__ __forceinline__ C2<double> div_v(const Geo<double>& G, const GridView
 template <class T, bool INIT>
 __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
   __shared__ double red[NT / 32 * 4];
-  const int slot = A.nblk2slot[blockIdx.x];
+  const int2 bm = A.nblk2slot[blockIdx.x];
+  const int slot = bm.x, lb = bm.y;
   SlotScalars* S = A.sc + slot;
   const bool pend = INIT;
   if (INIT ? !S->pending : !S->active) return;
@@ -1120,7 +1264,6 @@ __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
   const GridView& g = d.g;
   const Geo<T> G(g);
   const Geo<double> G64(g);
-  const int lb = blockIdx.x - d.blk_nodal0;
   const C2<T> xi(T(d.xi_re), T(d.xi_im));
   const C2<double> xi64(d.xi_re, d.xi_im);
   const double sc = 1.0 / S->inv_scale_prev;   // scale of this solve's right-hand side
@@ -1222,11 +1365,11 @@ struct ResidualPol {
 template <class TI>
 __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
   __shared__ StencilSmem<double> sm;
-  const int slot = A.blk2slot[blockIdx.x];
+  const int2 bm = A.blk2slot[blockIdx.x];
+  const int slot = bm.x, lb = bm.y;
   SlotScalars* S = A.sc + slot;
   if (S->done || S->active || S->pending) return;  // finished, or an inner solve is under way
   const SlotDesc d = A.slots[slot];
-  const int lb = blockIdx.x - d.blk_stencil0;
   int i0, j0, k0, k1;
   tile_of(d, lb, d.g.nz, i0, j0, k0, k1);
   ResidualPol<TI> pol(d.g);
@@ -1521,3 +1664,5 @@ static __global__ void k_rhs_norm2(const double* rhs, int64_t n, double* part) {
 }
 
 }  // namespace tem
+
+#include "stencil_tma.cuh"

@@ -84,8 +84,9 @@ struct tem_server {
   std::vector<SlotDesc> slots_h;
   std::vector<SlotScalars> sc_h;
   std::vector<int> owner;  // request ticket per slot, -1 when free
-  DevBuf slots_d, sc_d, part_d, ticket_d, counters_d, map_d;
-  int nblk_s = 0, nblk_u = 0, nblk_n = 0;
+  DevBuf slots_d, sc_d, part_d, ticket_d, counters_d, map_d, tmaps_d;
+  BlockCounts bc;               // sizes of the block lists
+  std::vector<char> in_maps;   // slots in the current block lists
   int part_stride = 4 * kMaxBlocksPerSlot;
   bool maps_dirty = true;
   std::deque<std::unique_ptr<Request>> queue;
@@ -98,9 +99,10 @@ struct tem_server {
     BatchArgs A;
     A.slots = slots_d.as<SlotDesc>();
     A.sc = sc_d.as<SlotScalars>();
-    A.blk2slot = map_d.as<int>();
-    A.ublk2slot = map_d.as<int>() + nblk_s;
-    A.nblk2slot = map_d.as<int>() + nblk_s + nblk_u;
+    A.blk2slot = map_d.as<int2>();
+    A.ublk2slot = map_d.as<int2>() + bc.s;
+    A.nblk2slot = map_d.as<int2>() + bc.s + bc.u;
+    A.tmaps = tmaps_d.as<CUtensorMap>();
     A.part = part_d.as<double>();
     A.ticket = ticket_d.as<unsigned>();
     A.n_active = counters_d.as<int>();
@@ -121,7 +123,7 @@ struct tem_server {
   size_t footprint(const Request& r) const {
     const int64_t nc = (int64_t)r.hx.size() * r.hy.size() * r.hz.size();
     const int64_t n1 = r.hx.size() + r.hy.size() + r.hz.size();
-    size_t b = 9 * n1 * 12 + 7 * nc * 12 + nc * 8;        // grid: geometry, masses, diag(K), sigma
+    size_t b = 9 * n1 * 12 + 7 * nc * 12 + nc * 8 + nc * 16;  // grid: geometry, masses, diag(K), sigma, packed masses
     b += 3 * nc * 8;                                         // f
     b += (size_t)r.s * slot_vector_bytes(nc, opt.solver.precision);
     b += 4096 + r.rx.size() * 16 * 8 + r.c.size() * 8 + (size_t)r.n_rx * r.K * 8;
@@ -201,6 +203,16 @@ struct tem_server {
       d.div_ny = make_fastdiv((uint32_t)d.g.ny);
       d.div_nynz = make_fastdiv((uint32_t)(d.g.ny * d.g.nz));
       decompose_slot(d, nodal);
+      d.tma = 0;
+      if (opt.solver.precision == TEM_PREC_MIXED && tma_stencil_enabled()) {
+        CUtensorMap tm[tma::NMAP];
+        if (encode_tile_maps(d, tm)) {
+          d.tma = 1;
+          TEM_CUDA_TRY(cudaMemcpyAsync(tmaps_d.as<CUtensorMap>() + (size_t)q * tma::NMAP, tm, sizeof(tm),
+                                       cudaMemcpyHostToDevice, s_));
+          TEM_CUDA_TRY(cudaStreamSynchronize(s_));   // tm lives on this stack frame
+        }
+      }
       SlotScalars S;
       std::memset(&S, 0, sizeof(S));
       S.max_iter = opt.solver.max_iter;
@@ -224,32 +236,24 @@ struct tem_server {
     return TEM_OK;
   }
 
+  // The slots to launch: those of running requests whose shifts have not finished.
+  std::vector<char> wanted_slots() const {
+    std::vector<char> use(owner.size(), 0);
+    for (size_t q = 0; q < owner.size(); ++q) use[q] = owner[q] >= 0 && !sc_h[q].done;
+    return use;
+  }
+
   int rebuild_maps() {
-    // block lists of every running slot; slot descriptors of the table
-    std::vector<int> ms, mu, mn;
-    for (int q = 0; q < (int)owner.size(); ++q) {
-      if (owner[q] < 0) continue;
-      SlotDesc& d = slots_h[q];
-      d.blk_stencil0 = (int)ms.size();
-      d.blk_update0 = (int)mu.size();
-      d.blk_nodal0 = (int)mn.size();
-      ms.insert(ms.end(), d.nblk_stencil, q);
-      mu.insert(mu.end(), d.nblk_update, q);
-      mn.insert(mn.end(), d.nblk_nodal, q);
-    }
-    nblk_s = (int)ms.size();
-    nblk_u = (int)mu.size();
-    nblk_n = (int)mn.size();
-    std::vector<int> map;
-    map.reserve(ms.size() + mu.size() + mn.size());
-    map.insert(map.end(), ms.begin(), ms.end());
-    map.insert(map.end(), mu.begin(), mu.end());
-    map.insert(map.end(), mn.begin(), mn.end());
-    if (map.empty()) map.push_back(0);
-    if (map_d.bytes < map.size() * sizeof(int)) TEM_TRY(map_d.alloc(2 * map.size() * sizeof(int), st));
-    TEM_CUDA_TRY(cudaMemcpyAsync(map_d.ptr, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    // interleaved block lists of the wanted slots; slot descriptors of the table
+    in_maps = wanted_slots();
+    std::vector<int2> map;
+    build_block_maps(slots_h, in_maps, map, &bc);
+    if (map.empty()) map.push_back(make_int2(0, 0));
+    if (map_d.bytes < map.size() * sizeof(int2)) TEM_TRY(map_d.alloc(2 * map.size() * sizeof(int2), st));
+    TEM_CUDA_TRY(cudaMemcpyAsync(map_d.ptr, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
     TEM_CUDA_TRY(cudaMemcpyAsync(slots_d.ptr, slots_h.data(), slots_h.size() * sizeof(SlotDesc),
                                  cudaMemcpyHostToDevice, st));
+    TEM_CUDA_TRY(cudaStreamSynchronize(st));   // map lives on this stack frame
     maps_dirty = false;
     return TEM_OK;
   }
@@ -257,13 +261,13 @@ struct tem_server {
   int launch_residual_and_start() {
     BatchArgs A = args();
     int* n_done = counters_d.as<int>() + 1;
-    if (nblk_s == 0) return TEM_OK;
+    if (bc.s == 0) return TEM_OK;
     if (opt.solver.precision == TEM_PREC_FP64) {
-      k_residual<double><<<nblk_s, NT, 0, st>>>(A, n_done);
-      if (nodal) k_cocg_nodal<double, true><<<nblk_n, NT, 0, st>>>(A);
+      k_residual<double><<<bc.s, NT, 0, st>>>(A, n_done);
+      if (nodal) k_cocg_nodal<double, true><<<bc.n, NT, 0, st>>>(A);
     } else {
-      k_residual<float><<<nblk_s, NT, 0, st>>>(A, n_done);
-      if (nodal) k_cocg_nodal<float, true><<<nblk_n, NT, 0, st>>>(A);
+      k_residual<float><<<bc.s, NT, 0, st>>>(A, n_done);
+      if (nodal) k_cocg_nodal<float, true><<<bc.n, NT, 0, st>>>(A);
     }
     count_launch(nodal ? 2 : 1);
     TEM_CUDA_TRY(cudaGetLastError());
@@ -272,17 +276,16 @@ struct tem_server {
 
   int launch_iteration() {
     BatchArgs A = args();
-    if (nblk_s == 0) return TEM_OK;
+    if (bc.s == 0) return TEM_OK;
     if (opt.solver.precision == TEM_PREC_FP64) {
-      k_cocg_stencil<double><<<nblk_s, NT, 0, st>>>(A);
-      k_cocg_update<double><<<nblk_u, NT, 0, st>>>(A);
-    } else {
-      TEM_CUDA_TRY(launch_stencil_pipe(A, nblk_s, st));
-      k_cocg_update<float><<<nblk_u, NT, 0, st>>>(A);
+      k_cocg_stencil<double><<<bc.s, NT, 0, st>>>(A);
+      k_cocg_update<double><<<bc.u, NT, 0, st>>>(A);
+      count_launch(2);
+      TEM_CUDA_TRY(cudaGetLastError());
+      return TEM_OK;
     }
-    count_launch(2);
-    TEM_CUDA_TRY(cudaGetLastError());
-    return TEM_OK;
+    TEM_TRY(launch_pass_a_f32(A, bc, st));
+    return launch_pass_b_f32(A, bc, st);
   }
 
   int finish(Request& r) {
@@ -347,7 +350,7 @@ struct tem_server {
       queue.pop_front();
     }
     if (running.empty()) return TEM_OK;
-    if (maps_dirty) TEM_TRY(rebuild_maps());
+    if (maps_dirty || wanted_slots() != in_maps) TEM_TRY(rebuild_maps());
     TEM_TRY(launch_residual_and_start());
     for (int it = 0; it < opt.iters_per_step; ++it) TEM_TRY(launch_iteration());
     TEM_TRY(launch_residual_and_start());
@@ -414,6 +417,7 @@ int tem_server_create(const tem_server_options* opt_in, void* cuda_stream, tem_s
   TEM_TRY(s->part_d.alloc((size_t)n * s->part_stride * sizeof(double), s->st));
   TEM_TRY(s->ticket_d.alloc(n * sizeof(unsigned), s->st));
   TEM_TRY(s->counters_d.alloc(2 * sizeof(int), s->st));
+  TEM_TRY(s->tmaps_d.alloc((size_t)n * tma::NMAP * sizeof(CUtensorMap), s->st));
   TEM_CUDA_TRY(cudaMemcpyAsync(s->sc_d.ptr, s->sc_h.data(), n * sizeof(SlotScalars), cudaMemcpyHostToDevice, s->st));
   TEM_CUDA_TRY(cudaMemsetAsync(s->ticket_d.ptr, 0, n * sizeof(unsigned), s->st));
   TEM_CUDA_TRY(cudaMemsetAsync(s->counters_d.ptr, 0, 2 * sizeof(int), s->st));

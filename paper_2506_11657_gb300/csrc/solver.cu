@@ -10,7 +10,11 @@
 //               to x in FP64 and recomputes r in FP64 (defect correction).
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
+
+#include <cudaTypedefs.h>
 
 #include "kernels.cuh"
 #include "solver.h"
@@ -62,6 +66,130 @@ void decompose_slot(SlotDesc& d, int nodal) {
   d.nblk_nodal = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (d.g.ncomp + NT * 8 - 1) / (NT * 8)));
 }
 
+// ---------------------------------------------------------------- block lists
+// The CTAs of every used slot, interleaved by block index: block b of slot 0, of slot 1, ...,
+// then block b+1.  Slots of one grid (the shifts of a model) then sweep the same tile at the same
+// time, so the grid's shared arrays (masses, diag K) come from L2 for all but the first.  The
+// stencil and update lists put the slots with d.tma first (their own launches).
+void build_block_maps(const std::vector<SlotDesc>& slots, const std::vector<char>& use, std::vector<int2>& map,
+                      BlockCounts* bc) {
+  map.clear();
+  const int ns = (int)slots.size();
+  auto one = [&](auto nblk_of, int cls) {   // cls: 1 tma slots only, 0 the others, -1 all
+    int most = 0;
+    for (int q = 0; q < ns; ++q)
+      if (use[q]) most = std::max(most, nblk_of(slots[q]));
+    const size_t start = map.size();
+    for (int b = 0; b < most; ++b)
+      for (int q = 0; q < ns; ++q)
+        if (use[q] && b < nblk_of(slots[q]) && (cls < 0 || (slots[q].tma != 0) == (cls == 1)))
+          map.push_back(make_int2(q, b));
+    return (int)(map.size() - start);
+  };
+  auto st = [](const SlotDesc& d) { return d.nblk_stencil; };
+  auto up = [](const SlotDesc& d) { return d.nblk_update; };
+  auto no = [](const SlotDesc& d) { return d.nblk_nodal; };
+  bc->s_fast = one(st, 1);
+  bc->s = bc->s_fast + one(st, 0);
+  bc->u_fast = one(up, 1);
+  bc->u = bc->u_fast + one(up, 0);
+  bc->n = one(no, -1);
+}
+
+// ------------------------------------------------------------ TMA tile maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+static bool encode(EncodeTiledFn f, CUtensorMap* m, int rank, const void* base, const cuuint64_t* dim,
+                   const cuuint64_t* stride, const cuuint32_t* box) {
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), dim, stride, box, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The seven tile maps of one FP32 slot (w, a0, a1, psi, b0, b1 and the packed masses), in the
+// order of tma::MAP_*.  A complex FP32 vector is addressed as floats: x runs over 2 nx floats,
+// so a box starting at column i0-2 starts at float 2 (i0-2), a multiple of 4 (16 bytes).
+// Returns false when the layout does not allow tile loads (odd nx) or encoding fails.
+bool encode_tile_maps(const SlotDesc& d, CUtensorMap* out) {
+  const GridView& g = d.g;
+  if (!tma_layout_ok(g) || !g.Mq) return false;
+  EncodeTiledFn f = encode_fn();
+  if (!f) return false;
+  const cuuint64_t nx = g.nx, ny = g.ny, nz = g.nz;
+  const cuuint64_t dv[4] = {2 * nx, ny, nz, 3}, sv[3] = {8 * nx, 8 * nx * ny, 8 * (cuuint64_t)g.ncomp};
+  const cuuint32_t bv[4] = {2 * tma::BX, tma::BY, 1, 3};
+  const cuuint64_t dn[3] = {2 * nx, ny, nz}, sn[2] = {8 * nx, 8 * nx * ny};
+  const cuuint32_t bn[3] = {2 * tma::BX, tma::BY, 1};
+  const cuuint64_t dm[4] = {4, nx, ny, nz}, sm[3] = {16, 16 * nx, 16 * nx * ny};
+  const cuuint32_t bmq[4] = {4, tma::MX, tma::MY, 1};
+  bool ok = encode(f, out + tma::MAP_W, 4, d.w, dv, sv, bv) && encode(f, out + tma::MAP_A0, 4, d.a0, dv, sv, bv) &&
+            encode(f, out + tma::MAP_A1, 4, d.a1, dv, sv, bv) && encode(f, out + tma::MAP_PSI, 3, d.psi, dn, sn, bn) &&
+            encode(f, out + tma::MAP_B0, 3, d.b0, dn, sn, bn) && encode(f, out + tma::MAP_B1, 3, d.b1, dn, sn, bn) &&
+            encode(f, out + tma::MAP_MQ, 4, g.Mq, dm, sm, bmq);
+  return ok;
+}
+
+// FP32 stencil kernel choice: the TMA kernel where every slot allows it, unless the environment
+// variable TEM_FP32_STENCIL=pipe selects the cp.async kernel (for comparisons).
+bool tma_stencil_enabled() {
+  static int on = -1;
+  if (on < 0) {
+    const char* v = std::getenv("TEM_FP32_STENCIL");
+    on = (v && std::strcmp(v, "pipe") == 0) ? 0 : 1;
+  }
+  return on == 1;
+}
+
+int launch_pass_a_f32(const BatchArgs& A, const BlockCounts& bc, cudaStream_t st) {
+  if (bc.s_fast > 0) {
+    TEM_CUDA_TRY(launch_stencil_tma(A, bc.s_fast, st));
+    count_launch();
+  }
+  if (bc.s > bc.s_fast) {
+    BatchArgs B = A;
+    B.blk2slot += bc.s_fast;
+    TEM_CUDA_TRY(launch_stencil_pipe(B, bc.s - bc.s_fast, st));
+    count_launch();
+  }
+  return TEM_OK;
+}
+
+int launch_pass_b_f32(const BatchArgs& A, const BlockCounts& bc, cudaStream_t st) {
+  if (bc.u_fast > 0) {
+    k_cocg_update_vec<<<bc.u_fast, NT, 0, st>>>(A);
+    TEM_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  if (bc.u > bc.u_fast) {
+    BatchArgs B = A;
+    B.ublk2slot += bc.u_fast;
+    k_cocg_update<float><<<bc.u - bc.u_fast, NT, 0, st>>>(B);
+    TEM_CUDA_TRY(cudaGetLastError());
+    count_launch();
+  }
+  return TEM_OK;
+}
+
+int stencil_f32_occupancy(bool use_tma) { return use_tma ? stencil_tma_occupancy() : stencil_pipe_occupancy(); }
+
 Batch::~Batch() {
   if (counters_h_) cudaFreeHost(counters_h_);
 }
@@ -103,28 +231,23 @@ int Batch::add_slot(const GridView& g, double xi_re, double xi_im, const SlotVec
 int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
   const int ns = (int)slots_h_.size();
   if (ns == 0) return TEM_EINVAL;
-  int blk_s = 0, blk_u = 0, blk_n = 0, max_part = 0;
+  int max_part = 0;
   for (auto& d : slots_h_) {
     decompose_slot(d, nodal_);
-    d.blk_stencil0 = blk_s;
-    d.blk_update0 = blk_u;
-    d.blk_nodal0 = blk_n;
-    blk_s += d.nblk_stencil;
-    blk_u += d.nblk_update;
-    blk_n += d.nblk_nodal;
     max_part = std::max(max_part, std::max(d.nblk_stencil, std::max(d.nblk_update, d.nblk_nodal)) * 4);
   }
-  nblk_stencil_ = blk_s;
-  nblk_update_ = blk_u;
-  nblk_nodal_ = blk_n;
   part_stride_ = max_part;
-  std::vector<int> map(blk_s + blk_u + blk_n);
-  for (int q = 0; q < ns; ++q) {
-    const SlotDesc& d = slots_h_[q];
-    for (int b = 0; b < d.nblk_stencil; ++b) map[d.blk_stencil0 + b] = q;
-    for (int b = 0; b < d.nblk_update; ++b) map[blk_s + d.blk_update0 + b] = q;
-    for (int b = 0; b < d.nblk_nodal; ++b) map[blk_s + blk_u + d.blk_nodal0 + b] = q;
+  std::vector<int2> map;
+  used_.assign(ns, 1);
+  // tile maps of the FP32 stencil pass (slots that cannot use them take the cp.async kernel)
+  std::vector<CUtensorMap> tm;
+  const bool want_tma = precision_ == TEM_PREC_MIXED && tma_stencil_enabled();
+  if (want_tma) {
+    tm.resize((size_t)ns * tma::NMAP);
+    for (int q = 0; q < ns; ++q)
+      slots_h_[q].tma = encode_tile_maps(slots_h_[q], tm.data() + (size_t)q * tma::NMAP) ? 1 : 0;
   }
+  build_block_maps(slots_h_, used_, map, &bc_);
   sc_h_.assign(ns, SlotScalars());
   for (int q = 0; q < ns; ++q) {
     SlotScalars& S = sc_h_[q];
@@ -143,13 +266,17 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
   }
   TEM_TRY(slots_d_.alloc(ns * sizeof(SlotDesc), st));
   TEM_TRY(sc_d_.alloc(ns * sizeof(SlotScalars), st));
-  TEM_TRY(map_d_.alloc(map.size() * sizeof(int), st));
+  TEM_TRY(map_d_.alloc(map.size() * sizeof(int2), st));
+  if (want_tma) {
+    TEM_TRY(tmaps_d_.alloc(tm.size() * sizeof(CUtensorMap), st));
+    TEM_CUDA_TRY(cudaMemcpyAsync(tmaps_d_.ptr, tm.data(), tm.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st));
+  }
   TEM_TRY(part_d_.alloc((size_t)ns * part_stride_ * sizeof(double), st));
   TEM_TRY(ticket_d_.alloc(ns * sizeof(unsigned), st));
   TEM_TRY(counters_d_.alloc(2 * sizeof(int), st));
   TEM_CUDA_TRY(cudaMemcpyAsync(slots_d_.ptr, slots_h_.data(), ns * sizeof(SlotDesc), cudaMemcpyHostToDevice, st));
   TEM_CUDA_TRY(cudaMemcpyAsync(sc_d_.ptr, sc_h_.data(), ns * sizeof(SlotScalars), cudaMemcpyHostToDevice, st));
-  TEM_CUDA_TRY(cudaMemcpyAsync(map_d_.ptr, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  TEM_CUDA_TRY(cudaMemcpyAsync(map_d_.ptr, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   TEM_CUDA_TRY(cudaMemsetAsync(ticket_d_.ptr, 0, ns * sizeof(unsigned), st));
   TEM_CUDA_TRY(cudaMemsetAsync(counters_d_.ptr, 0, 2 * sizeof(int), st));
   // zero every vector: boundary entries must read as 0 and are never written
@@ -162,13 +289,15 @@ int Batch::setup(const tem_options& opt, cudaStream_t st, const double* ff) {
 }
 
 static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& map, int nblk_s, int nblk_u,
-                           const DevBuf& part, const DevBuf& ticket, const DevBuf& counters, int stride) {
+                           const DevBuf& part, const DevBuf& ticket, const DevBuf& counters, int stride,
+                           const DevBuf& tmaps) {
   BatchArgs A;
   A.slots = slots.as<SlotDesc>();
   A.sc = sc.as<SlotScalars>();
-  A.blk2slot = map.as<int>();
-  A.ublk2slot = map.as<int>() + nblk_s;
-  A.nblk2slot = map.as<int>() + nblk_s + nblk_u;
+  A.blk2slot = map.as<int2>();
+  A.ublk2slot = map.as<int2>() + nblk_s;
+  A.nblk2slot = map.as<int2>() + nblk_s + nblk_u;
+  A.tmaps = tmaps.as<CUtensorMap>();
   A.part = part.as<double>();
   A.ticket = ticket.as<unsigned>();
   A.n_active = counters.as<int>();
@@ -177,36 +306,35 @@ static BatchArgs make_args(const DevBuf& slots, const DevBuf& sc, const DevBuf& 
 }
 
 int Batch::launch_stencil(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, bc_.s, bc_.u, part_d_, ticket_d_, counters_d_, part_stride_, tmaps_d_);
   if (precision_ == TEM_PREC_FP64) {
-    k_cocg_stencil<double><<<nblk_stencil_, NT, 0, st>>>(A);
+    k_cocg_stencil<double><<<bc_.s, NT, 0, st>>>(A);
     TEM_CUDA_TRY(cudaGetLastError());
-  } else {
-    TEM_CUDA_TRY(launch_stencil_pipe(A, nblk_stencil_, st));
+    count_launch();
+    return TEM_OK;
   }
-  count_launch();
-  return TEM_OK;
+  return launch_pass_a_f32(A, bc_, st);
 }
 
 int Batch::launch_update(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
-  if (precision_ == TEM_PREC_FP64)
-    k_cocg_update<double><<<nblk_update_, NT, 0, st>>>(A);
-  else
-    k_cocg_update<float><<<nblk_update_, NT, 0, st>>>(A);
-  count_launch();
-  TEM_CUDA_TRY(cudaGetLastError());
-  return TEM_OK;
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, bc_.s, bc_.u, part_d_, ticket_d_, counters_d_, part_stride_, tmaps_d_);
+  if (precision_ == TEM_PREC_FP64) {
+    k_cocg_update<double><<<bc_.u, NT, 0, st>>>(A);
+    count_launch();
+    TEM_CUDA_TRY(cudaGetLastError());
+    return TEM_OK;
+  }
+  return launch_pass_b_f32(A, bc_, st);
 }
 
 int Batch::launch_nodal(cudaStream_t st, int init_only) {
   if (!nodal_) return TEM_OK;
   if (!init_only) return TEM_EINVAL;  // the per-iteration nodal work is inside passes A and B
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, bc_.s, bc_.u, part_d_, ticket_d_, counters_d_, part_stride_, tmaps_d_);
   if (precision_ == TEM_PREC_FP64)
-    k_cocg_nodal<double, true><<<nblk_nodal_, NT, 0, st>>>(A);
+    k_cocg_nodal<double, true><<<bc_.n, NT, 0, st>>>(A);
   else
-    k_cocg_nodal<float, true><<<nblk_nodal_, NT, 0, st>>>(A);
+    k_cocg_nodal<float, true><<<bc_.n, NT, 0, st>>>(A);
   count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
@@ -217,15 +345,18 @@ int Batch::launch_iteration(cudaStream_t st) {
   return launch_update(st);
 }
 
-int Batch::launches_per_iteration() const { return 2; }
+int Batch::launches_per_iteration() const {
+  if (precision_ == TEM_PREC_FP64) return 2;
+  return (bc_.s_fast > 0) + (bc_.s > bc_.s_fast) + (bc_.u_fast > 0) + (bc_.u > bc_.u_fast);
+}
 
 int Batch::launch_residual(cudaStream_t st) {
-  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, nblk_stencil_, nblk_update_, part_d_, ticket_d_, counters_d_, part_stride_);
+  BatchArgs A = make_args(slots_d_, sc_d_, map_d_, bc_.s, bc_.u, part_d_, ticket_d_, counters_d_, part_stride_, tmaps_d_);
   int* n_done = counters_d_.as<int>() + 1;
   if (precision_ == TEM_PREC_FP64)
-    k_residual<double><<<nblk_stencil_, NT, 0, st>>>(A, n_done);
+    k_residual<double><<<bc_.s, NT, 0, st>>>(A, n_done);
   else
-    k_residual<float><<<nblk_stencil_, NT, 0, st>>>(A, n_done);
+    k_residual<float><<<bc_.s, NT, 0, st>>>(A, n_done);
   count_launch();
   TEM_CUDA_TRY(cudaGetLastError());
   return TEM_OK;
@@ -247,8 +378,14 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
   TEM_TRY(launch_nodal(st, 1));
   launches += 2;
   TEM_TRY(poll());
+  int done_seen = 0;
   int64_t rounds = 0;
   while (counters_h_[1] < ns) {
+    if (counters_h_[1] != done_seen) {
+      // some slots finished: launch only the others from now on
+      done_seen = counters_h_[1];
+      TEM_TRY(drop_done_slots(st));
+    }
     if (++rounds > max_rounds) return TEM_ETIMEOUT;
     if (counters_h_[0] > 0) {
       for (int it = 0; it < every; ++it) {
@@ -269,6 +406,18 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
     stats->launches += launches;
     stats->outer_steps += outer;
   }
+  return TEM_OK;
+}
+
+// Rebuild the block lists without the slots that are done (after a poll: nothing in flight).
+// A slot's blocks keep their block indices, so its arithmetic is unchanged.
+int Batch::drop_done_slots(cudaStream_t st) {
+  TEM_TRY(fetch_scalars(st));
+  for (size_t q = 0; q < sc_h_.size(); ++q) used_[q] = sc_h_[q].done ? 0 : 1;
+  std::vector<int2> map;
+  build_block_maps(slots_h_, used_, map, &bc_);
+  if (map.empty()) return TEM_OK;
+  TEM_CUDA_TRY(cudaMemcpyAsync(map_d_.ptr, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   return TEM_OK;
 }
 

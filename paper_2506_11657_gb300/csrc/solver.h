@@ -1,6 +1,8 @@
 // Batched shifted COCG driver: many (problem, shift) slots advanced together.
 #pragma once
 
+#include <cuda.h>
+
 #include "tem_internal.h"
 
 namespace tem {
@@ -22,6 +24,12 @@ struct SolveStats {
   int outer_steps = 0;
 };
 
+// Sizes of the block lists: stencil (s blocks, the first s_fast of slots with tma), update (u,
+// u_fast likewise), nodal (n).
+struct BlockCounts {
+  int s = 0, s_fast = 0, u = 0, u_fast = 0, n = 0;
+};
+
 class Batch {
  public:
   // Slots must be added before setup(); all share one precision.
@@ -40,9 +48,9 @@ class Batch {
   const std::vector<SlotDesc>& slots_host() const { return slots_h_; }
   int precision() const { return precision_; }
 
-  int stencil_blocks() const { return nblk_stencil_; }
-  int update_blocks() const { return nblk_update_; }
-  int nodal_blocks() const { return nblk_nodal_; }
+  int stencil_blocks() const { return bc_.s; }
+  int update_blocks() const { return bc_.u; }
+  int nodal_blocks() const { return bc_.n; }
   // launch one (stencil, update) pair or one residual pass for all slots (bench / profiling)
   int launch_iteration(cudaStream_t st);
   int launches_per_iteration() const;
@@ -50,17 +58,35 @@ class Batch {
   int launch_update(cudaStream_t st);
   int launch_nodal(cudaStream_t st, int init_only);
   int launch_residual(cudaStream_t st);
+  bool uses_tma() const { return bc_.s_fast > 0; }
 
  private:
+  int drop_done_slots(cudaStream_t st);
   int precision_;
   int nodal_;
   std::vector<SlotDesc> slots_h_;
   std::vector<SlotScalars> sc_h_;
-  int nblk_stencil_ = 0, nblk_update_ = 0, nblk_nodal_ = 0;
+  BlockCounts bc_;
   int part_stride_ = 0;
-  DevBuf slots_d_, sc_d_, map_d_, part_d_, ticket_d_, counters_d_;
+  DevBuf slots_d_, sc_d_, map_d_, part_d_, ticket_d_, counters_d_, tmaps_d_;
+  std::vector<char> used_;      // slots in the block lists
   int* counters_h_ = nullptr;   // pinned: [n_active, n_done]
 };
+
+struct BatchArgs;
+
+// Interleaved block lists (stencil | update | nodal) of the slots with use[q] != 0.
+void build_block_maps(const std::vector<SlotDesc>& slots, const std::vector<char>& use, std::vector<int2>& map,
+                      BlockCounts* bc);
+// FP32 passes A and B over the block lists: the TMA stencil and the 16-byte update over the
+// slots with tma, the cp.async stencil and the scalar update over the others (one launch each
+// part that has blocks).  Returns a status; counts its launches.
+int launch_pass_a_f32(const BatchArgs& A, const BlockCounts& bc, cudaStream_t st);
+int launch_pass_b_f32(const BatchArgs& A, const BlockCounts& bc, cudaStream_t st);
+// Tile maps (tma::NMAP of them) of an FP32 slot; false if the slot cannot use tile loads.
+bool encode_tile_maps(const SlotDesc& d, CUtensorMap* out);
+bool tma_stencil_enabled();
+int stencil_f32_occupancy(bool use_tma);
 
 // process-wide count of kernels launched by the library
 void count_launch(int n = 1);

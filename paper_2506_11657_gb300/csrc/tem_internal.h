@@ -71,6 +71,8 @@ struct GridView {
   const float* Wnf;         // FP32 copy
   const double* dK;         // [3][ncomp] diag(K) per edge, 0 on boundary/padding entries
   const float* dKf;         // FP32 copy
+  const float4* Mq;         // [ncomp] per node (M_x, M_y, M_z, W_n) in FP32: the masses of the three
+                            // edges leaving the node and its nodal weight, one 16-byte record
 };
 
 }  // namespace tem
@@ -83,6 +85,7 @@ struct tem_grid {
   tem::DevBuf geo;                  // packed 1-D arrays
   tem::DevBuf me;                   // Me, Wn, dK (FP64) then Mef, Wnf, dKf (FP32)
   tem::DevBuf sig;                  // sigma on the device (FP64)
+  tem::DevBuf mq;                   // packed FP32 (M_x, M_y, M_z, W_n) per node
   int device = 0;
 };
 
@@ -144,9 +147,7 @@ struct SlotDesc {
   int nblk_stencil;         // tiles_x*tiles_y*zchunks
   int nblk_update;          // blocks of the update pass
   int nblk_nodal;           // blocks of the nodal pass
-  int blk_stencil0;         // first global block of this slot in the stencil launch
-  int blk_update0;          // first global block of this slot in the update launch
-  int blk_nodal0;           // first global block of this slot in the nodal launch
+  int tma;                  // 1: the FP32 stencil pass may use this slot's tile maps (even nx)
   FastDiv div_nx, div_ny, div_nynz;
   // defect correction (FP64 outer loop)
   const double* f;          // right-hand side, real, edge layout (FP64)

@@ -100,8 +100,8 @@ def test_default_options_and_struct_layout(lib):
     o = lib.Options()
     C.memset(C.byref(o), 0x7f, C.sizeof(o))
     lib.lib().tem_default_options(C.byref(o))
-    assert (o.precision, o.max_iter, o.tol, o.inner_tol) == (lib.PREC_FP64, 20000, 1e-12, 1e-3)
-    assert (o.max_outer, o.check_every, o.keep_state, o.precond, o.carry_direction) == (40, 32, 0, 0, 0)
+    assert (o.precision, o.max_iter, o.tol, o.inner_tol) == (lib.PREC_FP64, 20000, 1e-12, 1e-1)
+    assert (o.max_outer, o.check_every, o.keep_state, o.precond, o.carry_direction) == (40, 32, 0, 0, 1)
     assert C.sizeof(o) == 48
 
 
