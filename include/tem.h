@@ -132,7 +132,9 @@ int tem_build_grid(const double* hx, int64_t nx, const double* hy, int64_t ny,
                    const double* hz, int64_t nz, const double* origin,
                    const double* sigma, void* cuda_stream, tem_grid** out);
 
-/* Replace the conductivity of an existing grid (same sizes and rules as tem_build_grid). */
+/* Replace the conductivity of an existing grid (same sizes and rules as tem_build_grid).
+   A state kept by an earlier tem_forward on this grid belongs to the old conductivity: after
+   this call, tem_adjoint and tem_jvp on that state return TEM_EINVAL (run the forward again). */
 int tem_grid_set_sigma(tem_grid* grid, const double* sigma, void* cuda_stream);
 
 /* Grid sizes: dims[0..2] = nx, ny, nz; returns TEM_EINVAL on NULL. */
@@ -238,7 +240,8 @@ int tem_state_fields(const tem_state* state, int64_t k0, int64_t nk, void* cuda_
  *   lambda_i = (K - xi_i M)^{-1} w_i      (A_i is complex symmetric),
  *   grad[c] = sum_i Re( xi_i sum_{e in c} (sigma_c V_c / 4) lambda_i[e] x_i[e] ).
  * The adjoint solves use the precision and tolerances of the forward call.
- * Returns TEM_ENOCONV (gradient written) if an adjoint solve hit max_iter.
+ * Returns TEM_ENOCONV (gradient written) if an adjoint solve hit max_iter, TEM_EINVAL if the
+ * grid's conductivity was replaced (tem_grid_set_sigma) after the forward call.
  */
 int tem_adjoint(tem_state* state, const double* dphi_dd, void* cuda_stream, double* grad_logsigma_out);
 
@@ -252,8 +255,8 @@ int tem_adjoint(tem_state* state, const double* dphi_dd, void* cuda_stream, doub
  * precision and tolerances of the forward call; the nodal preconditioner adds the
  * divergence of b_i, which is not zero here).  J^T is tem_adjoint: the two satisfy
  * <g, J dm> = <tem_adjoint(g), dm>.  A zero direction returns zeros without a solve.
- * Returns TEM_EINVAL for NULL pointers or a non-finite entry of dm, TEM_ENOCONV (output
- * written) if a solve hit max_iter.
+ * Returns TEM_EINVAL for NULL pointers, a non-finite entry of dm or a conductivity replaced
+ * after the forward call, TEM_ENOCONV (output written) if a solve hit max_iter.
  */
 int tem_jvp(tem_state* state, const double* dlogsigma, void* cuda_stream, double* ddbzdt_out);
 

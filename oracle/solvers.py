@@ -19,7 +19,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-__all__ = ["DenseEig", "solve_lu", "solve_cocg"]
+__all__ = ["DenseEig", "factor_lu", "solve_lu", "solve_cocg"]
 
 
 class DenseEig:
@@ -46,10 +46,15 @@ class DenseEig:
         return self.apply(fn, f)
 
 
+def factor_lu(K, Mdiag, shift):
+    """T1: the SuperLU factorisation of K - shift M in complex128 (its .solve(b) gives A^{-1} b)."""
+    A = (K.astype(np.complex128) - shift * sp.diags(np.asarray(Mdiag, dtype=np.complex128))).tocsc()
+    return spla.splu(A)
+
+
 def solve_lu(K, Mdiag, f, shift):
     """T1: x = (K - shift M)^{-1} f by SuperLU in complex128."""
-    A = (K.astype(np.complex128) - shift * sp.diags(np.asarray(Mdiag, dtype=np.complex128))).tocsc()
-    return spla.splu(A).solve(np.asarray(f, dtype=np.complex128))
+    return factor_lu(K, Mdiag, shift).solve(np.asarray(f, dtype=np.complex128))
 
 
 def solve_cocg(K, Mdiag, f, shift, tol=1e-13, maxiter=20000, x0=None):

@@ -25,7 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 from .yee import YeeGrid
-from .solvers import solve_lu, solve_cocg, DenseEig
+from .solvers import factor_lu, solve_cocg, DenseEig
 
 __all__ = ["TEMProblem"]
 
@@ -47,14 +47,23 @@ class TEMProblem:
         rx = np.atleast_2d(np.asarray(rx_xyz, dtype=np.float64))
         self.Q = np.stack([g.receiver_row(*p)[mask] for p in rx])  # (n_rx, N)
         self._dMdm = None
+        self._lu = {}
 
     @property
     def n(self):
         return self.K.shape[0]
 
+    def _lu_solve(self, b, shift):
+        """(K - shift M)^{-1} b by sparse LU; one factorisation per shift, kept for later right-hand
+        sides of the same shift (the adjoint and linearised solves reuse the forward's)."""
+        key = complex(shift)
+        if key not in self._lu:
+            self._lu[key] = factor_lu(self.K, self.Md, key)
+        return self._lu[key].solve(np.asarray(b, dtype=np.complex128))
+
     def solve(self, shift, method="lu", tol=1e-13):
         if method == "lu":
-            return solve_lu(self.K, self.Md, self.f, shift)
+            return self._lu_solve(self.f, shift)
         x, _, _ = solve_cocg(self.K, self.Md, self.f, shift, tol=tol)
         return x
 
@@ -85,7 +94,7 @@ class TEMProblem:
         for i, s in enumerate(shifts):
             w = beta[i] @ self.Q
             if method == "lu":
-                lam = solve_lu(self.K, self.Md, w, s)
+                lam = self._lu_solve(w, s)
             else:
                 lam, _, _ = solve_cocg(self.K, self.Md, w, s)
             g += (s * (D.T @ (lam * xs[i]))).real
@@ -103,7 +112,7 @@ class TEMProblem:
         for i, s in enumerate(shifts):
             b = s * (dM * xs[i])
             if method == "lu":
-                dx = solve_lu(self.K, self.Md, b, s)
+                dx = self._lu_solve(b, s)
             else:
                 dx, _, _ = solve_cocg(self.K, self.Md, b, s)
             y.append(self.Q @ dx)

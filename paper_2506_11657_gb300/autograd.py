@@ -4,6 +4,12 @@ Forward: tem_grid_set_sigma(exp(log_sigma)) + tem_forward (solutions kept).
 Backward: tem_adjoint with the incoming gradient dphi/dd, returning dphi/dlog sigma
 (Sec. 4: the Jacobian-transpose product through the shifted solves).
 All arithmetic runs in libtem.so; this module only moves arrays.
+
+The kept solutions belong to the conductivity of their forward call.  When another forward
+has changed the grid's conductivity before this backward (two loss terms on one grid, a line
+search), the library refuses the stale state; backward then sets this call's conductivity
+again and repeats the forward solve before the adjoint.  The state stays alive with the graph,
+so backward may run more than once (retain_graph).
 """
 from __future__ import annotations
 
@@ -18,18 +24,27 @@ class TEMForward(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, log_sigma, grid, loop_xy, z_loop, rx, shifts, c, options):
-        ls = log_sigma.detach().to("cpu", torch.float64).numpy().ravel()
+        ls = log_sigma.detach().to("cpu", torch.float64).numpy().ravel().copy()
         grid.set_sigma(np.exp(ls))
         res = tem.forward(grid, loop_xy, z_loop, rx, shifts, c, options, keep_state=True)
         ctx.state = res.state
+        ctx.args = (grid, loop_xy, z_loop, rx, shifts, c, options, ls)
         ctx.shape = log_sigma.shape
         return torch.from_numpy(res.d.copy()).to(log_sigma.device)
 
     @staticmethod
     def backward(ctx, grad_d):
         g = grad_d.detach().to("cpu", torch.float64).numpy()
-        grad = ctx.state.adjoint(g)
-        ctx.state.close()
+        try:
+            grad = ctx.state.adjoint(g)
+        except tem.TEMError as e:
+            if e.code != tem.TEM_EINVAL:
+                raise
+            grid, loop_xy, z_loop, rx, shifts, c, options, ls = ctx.args
+            grid.set_sigma(np.exp(ls))
+            ctx.state.close()
+            ctx.state = tem.forward(grid, loop_xy, z_loop, rx, shifts, c, options, keep_state=True).state
+            grad = ctx.state.adjoint(g)
         out = torch.from_numpy(grad).reshape(ctx.shape).to(grad_d.device)
         return out, None, None, None, None, None, None, None
 

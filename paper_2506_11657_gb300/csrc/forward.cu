@@ -20,6 +20,7 @@ using namespace tem;
 
 struct tem_state {
   const tem_grid* grid = nullptr;
+  uint64_t sigma_gen = 0;                   // the grid's conductivity generation at the forward call
   tem_options opt;
   int s = 0, K = 0, n_rx = 0;
   std::vector<double> xi, c;                // host copies
@@ -112,6 +113,7 @@ int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
   TEM_TRY(build_source(grid, loop_xy, n_vertices, z_loop, current, fterms));
   std::unique_ptr<tem_state> S(new tem_state());
   S->grid = grid;
+  S->sigma_gen = grid->sigma_gen;
   S->opt = opt;
   S->s = int(s);
   S->K = int(K);
@@ -329,6 +331,10 @@ int tem_state_fields(const tem_state* state, int64_t k0, int64_t nk, void* cuda_
 
 int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) {
   if (!S || !g || !grad || !S->batch) return TEM_EINVAL;
+  if (S->grid->sigma_gen != S->sigma_gen) {
+    set_last_error("tem_adjoint: the grid's conductivity changed after the forward call", __FILE__, __LINE__);
+    return TEM_EINVAL;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   for (int64_t q = 0; q < (int64_t)S->n_rx * S->K; ++q)
     if (!std::isfinite(g[q])) return TEM_EINVAL;
@@ -408,6 +414,10 @@ int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) 
 
 int tem_jvp(tem_state* S, const double* dlogsigma, void* cuda_stream, double* ddbzdt_out) {
   if (!S || !dlogsigma || !ddbzdt_out || !S->batch) return TEM_EINVAL;
+  if (S->grid->sigma_gen != S->sigma_gen) {
+    set_last_error("tem_jvp: the grid's conductivity changed after the forward call", __FILE__, __LINE__);
+    return TEM_EINVAL;
+  }
   const tem_grid* grid = S->grid;
   const int64_t ncomp = grid->v.ncomp;
   bool any = false;

@@ -183,6 +183,7 @@ static int upload_sigma(tem_grid* g, const double* sigma, cudaStream_t st) {
   const int64_t ncell = g->v.ncomp;
   if (!sigma || !finite_positive(sigma, ncell)) return TEM_EINVAL;
   g->sigma.assign(sigma, sigma + ncell);
+  g->sigma_gen += 1;
   TEM_CUDA_TRY(cudaMemcpyAsync(g->sig.ptr, sigma, ncell * sizeof(double), cudaMemcpyHostToDevice, st));
   // layout: Me (3n), Wn (n), dK (3n) doubles, then Mef (3n), Wnf (n), dKf (3n) floats
   double* Me = g->me.as<double>();

@@ -284,7 +284,7 @@ struct tem_server {
       TEM_CUDA_TRY(cudaGetLastError());
       return TEM_OK;
     }
-    TEM_TRY(launch_pass_a_f32(A, bc, st));
+    TEM_TRY(launch_pass_a_f32(A, bc, nodal != 0, st));
     return launch_pass_b_f32(A, bc, st);
   }
 

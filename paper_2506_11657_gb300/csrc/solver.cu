@@ -58,7 +58,7 @@ void decompose_slot(SlotDesc& d, int nodal) {
   // the longest z chunk (64/32/16/8 planes) that gives the slot alone 2 CTAs per SM (152 SMs)
   const int64_t cols = (int64_t)d.tiles_x * d.tiles_y;
   d.zchunk = ZMAX;
-  while (d.zchunk > 8 && cols * ((d.g.nz + d.zchunk - 1) / d.zchunk) < 2 * 152) d.zchunk /= 2;
+  while (d.zchunk > 8 && cols * ((d.g.nz + d.zchunk - 1) / d.zchunk) < TEM_SLOT_CTAS_PER_SM * 152) d.zchunk /= 2;
   d.zchunks = (d.g.nz + d.zchunk - 1) / d.zchunk;
   d.nblk_stencil = d.tiles_x * d.tiles_y * d.zchunks;
   const int64_t n = 3 * d.g.ncomp + (nodal ? d.g.ncomp : 0);
@@ -158,9 +158,9 @@ bool tma_stencil_enabled() {
   return on == 1;
 }
 
-int launch_pass_a_f32(const BatchArgs& A, const BlockCounts& bc, cudaStream_t st) {
+int launch_pass_a_f32(const BatchArgs& A, const BlockCounts& bc, bool nodal, cudaStream_t st) {
   if (bc.s_fast > 0) {
-    TEM_CUDA_TRY(launch_stencil_tma(A, bc.s_fast, st));
+    TEM_CUDA_TRY(launch_stencil_tma(A, bc.s_fast, nodal, st));
     count_launch();
   }
   if (bc.s > bc.s_fast) {
@@ -313,7 +313,7 @@ int Batch::launch_stencil(cudaStream_t st) {
     count_launch();
     return TEM_OK;
   }
-  return launch_pass_a_f32(A, bc_, st);
+  return launch_pass_a_f32(A, bc_, nodal_ != 0, st);
 }
 
 int Batch::launch_update(cudaStream_t st) {

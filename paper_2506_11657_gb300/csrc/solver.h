@@ -81,7 +81,7 @@ void build_block_maps(const std::vector<SlotDesc>& slots, const std::vector<char
 // FP32 passes A and B over the block lists: the TMA stencil and the 16-byte update over the
 // slots with tma, the cp.async stencil and the scalar update over the others (one launch each
 // part that has blocks).  Returns a status; counts its launches.
-int launch_pass_a_f32(const BatchArgs& A, const BlockCounts& bc, cudaStream_t st);
+int launch_pass_a_f32(const BatchArgs& A, const BlockCounts& bc, bool nodal, cudaStream_t st);
 int launch_pass_b_f32(const BatchArgs& A, const BlockCounts& bc, cudaStream_t st);
 // Tile maps (tma::NMAP of them) of an FP32 slot; false if the slot cannot use tile loads.
 bool encode_tile_maps(const SlotDesc& d, CUtensorMap* out);
@@ -95,6 +95,11 @@ void count_launch(int n = 1);
 // slot's grid, so a slot's arithmetic is the same in any batch.
 void decompose_slot(SlotDesc& d, int nodal);
 constexpr int kMaxBlocksPerSlot = 4096;
+// A slot's stencil decomposition takes the longest z chunk (64, 32, 16 or 8 planes) that still
+// gives the slot alone this many CTAs per SM (152 SMs).
+#ifndef TEM_SLOT_CTAS_PER_SM
+#define TEM_SLOT_CTAS_PER_SM 2
+#endif
 
 // An FP32 inner solve whose recursive residual has not reached a new minimum for this many
 // iterations ends, and the FP64 outer step restarts from the true residual.

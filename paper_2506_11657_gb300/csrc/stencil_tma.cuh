@@ -201,7 +201,8 @@ __device__ __forceinline__ void form_plane(const Ring& R, int sw, int so, const 
 // Rows of the box are 16-byte aligned only for an even nx; the tensor maps need that.
 __host__ __device__ inline bool tma_layout_ok(const GridView& g) { return (g.nx % 2) == 0; }
 
-static __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
+template <bool NODAL>
+__global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
   using namespace tma;
   extern __shared__ unsigned char smem_raw[];
   Ring R;
@@ -218,7 +219,7 @@ static __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) 
   tile_of(d, lb, nz, i0, j0, k0, k1);
   const CUtensorMap* maps = A.tmaps + (int64_t)slot * NMAP;
   const bool use_beta = !(S->beta_re == 0.0 && S->beta_im == 0.0);
-  const bool nodal = d.nodal != 0;
+  constexpr bool nodal = NODAL;   // the same for every slot of a launch
   const int par = S->parity;
   const int aold = par ? MAP_A1 : MAP_A0, bold = par ? MAP_B1 : MAP_B0;
   float4* anew = static_cast<float4*>(par ? d.a0 : d.a1);
@@ -441,28 +442,36 @@ static __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) 
   }
 }
 
-// Launch pass A through the TMA kernel (dynamic shared memory above 48 KB).
-static inline cudaError_t launch_stencil_tma(const BatchArgs& A, int nblk, cudaStream_t st) {
+// Launch pass A through the TMA kernel (dynamic shared memory above 48 KB); nodal: the
+// preconditioner of every slot in the launch has the nodal part.
+static inline cudaError_t launch_stencil_tma(const BatchArgs& A, int nblk, bool nodal, cudaStream_t st) {
   static bool attr_done[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_cocg_stencil_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_B);
+    cudaError_t e = cudaFuncSetAttribute(k_cocg_stencil_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tma::SMEM_B);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_cocg_stencil_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tma::SMEM_B);
     if (e != cudaSuccess) return e;
     attr_done[dev] = true;
   }
-  k_cocg_stencil_tma<<<nblk, NT, tma::SMEM_B, st>>>(A);
+  if (nodal)
+    k_cocg_stencil_tma<true><<<nblk, NT, tma::SMEM_B, st>>>(A);
+  else
+    k_cocg_stencil_tma<false><<<nblk, NT, tma::SMEM_B, st>>>(A);
   return cudaGetLastError();
 }
 
 // Resident CTAs per SM of the TMA stencil (0 on error).
 static inline int stencil_tma_occupancy() {
   int n = 0;
-  if (cudaFuncSetAttribute(k_cocg_stencil_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma::SMEM_B) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(k_cocg_stencil_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)tma::SMEM_B) != cudaSuccess)
     return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cocg_stencil_tma, NT, tma::SMEM_B) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cocg_stencil_tma<true>, NT, tma::SMEM_B) != cudaSuccess)
+    return 0;
   return n;
 }
 

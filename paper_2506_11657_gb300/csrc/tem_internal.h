@@ -86,6 +86,7 @@ struct tem_grid {
   tem::DevBuf me;                   // Me, Wn, dK (FP64) then Mef, Wnf, dKf (FP32)
   tem::DevBuf sig;                  // sigma on the device (FP64)
   tem::DevBuf mq;                   // packed FP32 (M_x, M_y, M_z, W_n) per node
+  uint64_t sigma_gen = 0;           // incremented by every conductivity upload
   int device = 0;
 };
 

@@ -155,8 +155,9 @@ def randblock128(n=128, seed=3):
                  channel_times(1e-5, 1e-2, 31), 20, meta={"seed": seed})
 
 
-def adjoint96(n=96, seed=5, n_rx_side=8):
-    h = 10.0
+def adjoint96(n=96, seed=5, n_rx_side=8, h=10.0, blocks=True):
+    """The adjoint-gradient model; n cells of h metres per side (n * h = 960 m keeps the physical
+    model: n=24, h=40 is its 4x coarsening); blocks=False gives the layered background."""
     air = n // 6
     hx = np.full(n, h)
     origin = (-(n // 2) * h, -(n // 2) * h, -(n - air) * h)
@@ -166,8 +167,8 @@ def adjoint96(n=96, seed=5, n_rx_side=8):
     rho[(zc > -30.0) & (zc < 0.0)] = 100.0
     rng = np.random.default_rng(seed)
     X, Y = np.meshgrid(xc, xc, indexing="xy")
-    for _ in range(4):
-        bw = rng.integers(4, 10, size=3) * h
+    for _ in range(4 if blocks else 0):
+        bw = rng.integers(4, 10, size=3) * 10.0
         cx, cy = rng.uniform(-150, 150, size=2)
         top = -rng.uniform(30, 120)
         r = 10.0 ** rng.uniform(np.log10(5.0), np.log10(50.0))
@@ -182,7 +183,7 @@ def adjoint96(n=96, seed=5, n_rx_side=8):
     RX, RY = np.meshgrid(off, off, indexing="xy")
     rx = np.stack((RX.ravel(), RY.ravel(), np.zeros(RX.size)), axis=1)
     return Model(f"adjoint{n}", hx, hx.copy(), hx.copy(), origin, sigma, loop, 0.0, rx,
-                 channel_times(1e-5, 1e-2, 31), 20, meta={"seed": seed})
+                 channel_times(1e-5, 1e-2, 31), 20, meta={"seed": seed, "h": h, "blocks": blocks})
 
 
 def serving_stream(n_requests=256, seed=4, rate=1.0, sizes=(32, 48, 64, 96)):

@@ -89,3 +89,34 @@ def test_autograd_function_backward(problem):
     assert np.allclose(out.detach().numpy(), d, rtol=1e-6, atol=1e-10 * np.abs(d).max())
     (out * torch.from_numpy(g)).sum().backward()
     assert np.abs(ls.grad.numpy() - grad).max() <= 1e-7 * np.abs(grad).max()
+
+
+def test_stale_state_is_refused_and_autograd_recovers(problem):
+    """A kept state belongs to the conductivity of its forward call: after tem_grid_set_sigma the
+    library refuses tem_adjoint and tem_jvp on it, and the autograd wrapper, given two forwards on
+    one grid before either backward, still returns both gradients."""
+    from paper_2506_11657_gb300 import tem
+    from paper_2506_11657_gb300.autograd import tem_forward_logsigma
+    m, rx, shifts, c, d, g, grad = problem
+    opt = tem.default_options(tol=1e-13)
+    grid = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma)
+    res = tem.forward(grid, m.loop_xy, m.z_loop, rx, shifts, c, opt, keep_state=True)
+    grid.set_sigma(m.sigma * 1.5)
+    for call in (lambda: res.state.adjoint(g), lambda: res.state.jvp(np.ones(m.sigma.size))):
+        with pytest.raises(tem.TEMError) as e:
+            call()
+        assert e.value.code == tem.TEM_EINVAL
+    res.state.close()
+    ls1 = torch.tensor(np.log(m.sigma.ravel()), dtype=torch.float64, requires_grad=True)
+    ls2 = torch.tensor(np.log(m.sigma.ravel() * 1.5), dtype=torch.float64, requires_grad=True)
+    o1 = tem_forward_logsigma(ls1, grid, m.loop_xy, m.z_loop, rx, shifts, c, opt)
+    o2 = tem_forward_logsigma(ls2, grid, m.loop_xy, m.z_loop, rx, shifts, c, opt)
+    gt = torch.from_numpy(g)
+    ((o1 * gt).sum() + (o2 * gt).sum()).backward()
+    assert np.abs(ls1.grad.numpy() - grad).max() <= 1e-7 * np.abs(grad).max()
+    grid.set_sigma(m.sigma * 1.5)
+    r2 = tem.forward(grid, m.loop_xy, m.z_loop, rx, shifts, c, opt, keep_state=True)
+    g2 = r2.state.adjoint(g)
+    r2.state.close()
+    assert np.abs(ls2.grad.numpy() - g2).max() <= 1e-9 * np.abs(g2).max()
+    grid.close()

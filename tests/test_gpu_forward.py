@@ -32,11 +32,8 @@ def _oracle(m, shifts, c, rx=None):
 
 
 def _check(d_gpu, d_ref, S, rel, floor):
-    bound = rel * np.abs(d_ref) + floor * S
-    err = np.abs(d_gpu - d_ref)
-    worst = np.max(err / bound)
-    assert worst <= 1.0, f"worst err/bound {worst:.3g}; max rel err {np.max(err / np.abs(d_ref)):.3g}"
-    return err / np.abs(d_ref)
+    from tests._parity import check
+    return check(d_gpu, d_ref, S, rel, floor, f"forward (rel {rel:g}, floor {floor:g})")
 
 
 @pytest.fixture(scope="module")

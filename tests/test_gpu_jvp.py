@@ -44,8 +44,8 @@ def problem():
 
 
 def _check(dd, ref, S, rel, floor):
-    worst = np.max(np.abs(dd - ref) / (rel * np.abs(ref) + floor * S))
-    assert worst <= 1.0, worst
+    from tests._parity import check
+    return check(dd, ref, S, rel, floor, f"J dm (rel {rel:g}, floor {floor:g})")
 
 
 @pytest.mark.parametrize("prec,rel,floor", [("fp64", 1e-6, 1e-10), ("mixed", 1e-5, 1e-9)])

@@ -28,8 +28,8 @@ def _oracle(m, shifts, c, rx):
 
 
 def _check(d, ref, S, rel, floor):
-    worst = np.max(np.abs(d - ref) / (rel * np.abs(ref) + floor * S))
-    assert worst <= 1.0, worst
+    from tests._parity import check
+    return check(d, ref, S, rel, floor, f"limits (rel {rel:g}, floor {floor:g})")
 
 
 @pytest.fixture(scope="module")

@@ -1,6 +1,7 @@
 """GPU tests of the continuous-batching server (tem_server_*).
 
 * a request's result is bitwise the same alone, in a mix, and through tem_forward;
+* every served result matches the oracle's response for the same shifts and weights;
 * a request that arrives while another runs is admitted before the first finishes and the
   two overlap on the device;
 * an HBM budget that holds one request at a time makes the second wait;
@@ -60,6 +61,22 @@ def test_alone_mixed_and_forward_agree_bitwise(setup):
         ref = tem.forward(grid, m.loop_xy, m.z_loop, m.rx, poles[i][0], poles[i][1],
                           tem.default_options(precision="mixed")).d
         assert np.array_equal(ref, mixed[i][0]), i
+
+
+def test_served_results_match_the_oracle(setup):
+    """Each served result -- the three requests in one mix, and each alone -- against the
+    oracle's sparse-LU response for the same shifts and weights, with the bound of the mixed
+    forward tests (rel 1e-5, cancellation floor 1e-9 S_k)."""
+    from tests._parity import check, oracle_responses
+    tem, models, poles = setup
+    refs = oracle_responses([(m, poles[i][0], poles[i][1], None) for i, m in enumerate(models)])
+    mixed = _run(tem.Server(iters_per_step=16), models, poles)
+    for i, m in enumerate(models):
+        alone = _run(tem.Server(iters_per_step=16), [m], [poles[i]])[0]
+        d_ref, S = refs[i]
+        for label, res in (("mixed", mixed[i]), ("alone", alone)):
+            assert res[1]["status"] == tem.TEM_OK
+            check(res[0], d_ref, S, 1e-5, 1e-9, f"served {label} model {i}")
 
 
 def test_late_request_is_admitted_while_another_runs(setup):

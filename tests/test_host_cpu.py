@@ -11,38 +11,71 @@ torch = pytest.importorskip("torch")
 from paper_2506_11657_gb300 import workloads as W
 
 
-def test_autograd_backward_is_the_adjoint(monkeypatch):
-    """With a linear stand-in d = A log sigma, backward must return A^T g and close the state."""
+def _standin(monkeypatch, A):
+    """A linear stand-in d = A log sigma whose kept state, like the library's, refuses an adjoint
+    once the grid's conductivity has changed after its forward call."""
     from paper_2506_11657_gb300 import autograd
-    rng = np.random.default_rng(2)
-    A = rng.standard_normal((2 * 5, 12))
-    closed = []
-
-    class State:
-        def adjoint(self, g):
-            return A.T @ np.asarray(g).ravel()
-
-        def close(self):
-            closed.append(True)
+    calls = {"forward": 0, "closed": 0}
 
     class Grid:
         def set_sigma(self, s):
             self.ls = np.log(s)
 
-    grid = Grid()
+    class State:
+        def __init__(self, grid):
+            self.grid, self.ls = grid, grid.ls.copy()
+
+        def adjoint(self, g):
+            if not np.array_equal(self.grid.ls, self.ls):
+                raise autograd.tem.TEMError(autograd.tem.TEM_EINVAL, "tem_adjoint")
+            return A.T @ np.asarray(g).ravel()
+
+        def close(self):
+            calls["closed"] += 1
 
     def forward(g, loop_xy, z_loop, rx, shifts, c, options, keep_state=False):
         assert keep_state
-        return types.SimpleNamespace(d=(A @ g.ls).reshape(2, 5), status=0, state=State())
+        calls["forward"] += 1
+        return types.SimpleNamespace(d=(A @ g.ls).reshape(2, 5), status=0, state=State(g))
 
     monkeypatch.setattr(autograd.tem, "forward", forward)
+    monkeypatch.setattr(autograd.tem, "last_error", lambda: "")
+    monkeypatch.setattr(autograd.tem, "status_string", lambda code: "EINVAL")
+    return autograd, Grid(), calls
+
+
+def test_autograd_backward_is_the_adjoint(monkeypatch):
+    """With a linear stand-in d = A log sigma, backward must return A^T g, twice if asked."""
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((2 * 5, 12))
+    autograd, grid, calls = _standin(monkeypatch, A)
     ls = torch.tensor(rng.standard_normal(12), dtype=torch.float64, requires_grad=True)
     d = autograd.TEMForward.apply(ls, grid, None, 0.0, None, None, None, None)
     assert np.allclose(d.detach().numpy(), (A @ ls.detach().numpy()).reshape(2, 5))
     g = torch.tensor(rng.standard_normal((2, 5)), dtype=torch.float64)
-    (d * g).sum().backward()
+    (d * g).sum().backward(retain_graph=True)
     assert np.allclose(ls.grad.numpy(), A.T @ g.numpy().ravel())
-    assert closed == [True]
+    (d * g).sum().backward()
+    assert np.allclose(ls.grad.numpy(), 2 * A.T @ g.numpy().ravel())
+    assert calls["forward"] == 1
+
+
+def test_autograd_two_forwards_on_one_grid(monkeypatch):
+    """Two forwards on one grid before either backward: the first backward finds its state
+    stale, sets its own conductivity again and repeats the forward; both gradients are right."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((2 * 5, 12))
+    autograd, grid, calls = _standin(monkeypatch, A)
+    l1 = torch.tensor(rng.standard_normal(12), dtype=torch.float64, requires_grad=True)
+    l2 = torch.tensor(rng.standard_normal(12), dtype=torch.float64, requires_grad=True)
+    d1 = autograd.TEMForward.apply(l1, grid, None, 0.0, None, None, None, None)
+    d2 = autograd.TEMForward.apply(l2, grid, None, 0.0, None, None, None, None)
+    g1 = torch.tensor(rng.standard_normal((2, 5)), dtype=torch.float64)
+    g2 = torch.tensor(rng.standard_normal((2, 5)), dtype=torch.float64)
+    ((d1 * g1).sum() + (d2 * g2).sum()).backward()
+    assert np.allclose(l1.grad.numpy(), A.T @ g1.numpy().ravel())
+    assert np.allclose(l2.grad.numpy(), A.T @ g2.numpy().ravel())
+    assert calls["forward"] == 3 and calls["closed"] == 1
 
 
 class _FakeServer:
