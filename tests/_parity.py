@@ -2,8 +2,10 @@
 weights, solved in parallel processes, and the per-channel bound with its achieved margins.
 
 Parity is defined for fixed (xi, c): d[r, k] = sum_i Re(c[i, k] q_r^T (K - xi_i M)^{-1} f).
-The bound per channel is |d_gpu - d_oracle| <= rel |d_oracle| + floor S_k with
-S_k = sum_i |c[i, k] y_i|, y_i = q_r^T x_i (the size of the terms before they cancel).
+Every channel must meet |d_gpu - d_oracle| <= rel |d_oracle| (rel = 1e-6 for FP64 paths, 1e-5
+for mixed precision).  The printout adds the ratio to rel |d| + floor S_k, S_k =
+sum_i |c[i, k] y_i| with y_i = q_r^T x_i, which shows how far each channel is from the level
+where the cancellation among the pole terms would start to limit any FP64 computation.
 """
 import multiprocessing as mp
 import os
@@ -51,15 +53,16 @@ def oracle_responses(cases, processes=None):
 
 
 def check(d_gpu, d_ref, S, rel, floor, label=""):
-    """Assert the per-channel bound; print the achieved margin and the plain relative error."""
+    """Assert the plain relative error |d_gpu - d_oracle| / |d_oracle| <= rel on every channel;
+    print it beside the cancellation-aware ratio err / (rel |d| + floor S_k) as a diagnostic."""
     bound = rel * np.abs(d_ref) + floor * S
     err = np.abs(d_gpu - d_ref)
     ratio = err / bound
     plain = err / np.abs(d_ref)
-    print(f"parity {label}: worst err/bound {ratio.max():.3g}, max plain rel err {plain.max():.3g} "
-          f"(median {np.median(plain):.3g}), channels with plain rel err <= {rel:g}: "
-          f"{int((plain <= rel).sum())}/{plain.size}")
-    assert ratio.max() <= 1.0, f"{label}: worst err/bound {ratio.max():.3g}; max rel err {plain.max():.3g}"
+    print(f"parity {label}: max plain rel err {plain.max():.3g} (median {np.median(plain):.3g}), "
+          f"channels with plain rel err <= {rel:g}: {int((plain <= rel).sum())}/{plain.size}; "
+          f"worst err / (rel |d| + floor S) {ratio.max():.3g}")
+    assert plain.max() <= rel, f"{label}: max plain rel err {plain.max():.3g} > {rel:g}"
     return plain
 
 

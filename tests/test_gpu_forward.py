@@ -1,14 +1,12 @@
 """GPU parity of tem_forward (FP64 and mixed precision) against the oracle, plus failure paths.
 
 Parity is defined for fixed shifts and channel weights (both sides consume the same
-(xi, c)): d[r, k] = sum_i Re(c[i, k] q_r^T (K - xi_i M)^{-1} f).  Per channel the bound is
-
-    |d_gpu - d_oracle| <= rel * |d_oracle| + floor * S_k,   S_k = sum_i |c[i, k] y_i|,
-
-where y_i = q_r^T x_i.  The second term is the cancellation floor: late channels of a
-Dirichlet-bounded model sum terms that cancel to 1 part in gamma_k = S_k / |d_k| (up to
-~1e7 here), so an FP64 solve accurate to eps in every y_i can only promise eps * S_k there.
-FP64: rel = 1e-6, floor = 1e-10 (solves to 1e-13).  MIXED: rel = 1e-5, floor = 1e-9.
+(xi, c)): d[r, k] = sum_i Re(c[i, k] q_r^T (K - xi_i M)^{-1} f).  Every channel must meet the
+plain relative error |d_gpu - d_oracle| <= rel |d_oracle|: rel = 1e-6 for FP64 (solves to an
+FP64 residual of 1e-13), rel = 1e-5 for mixed precision (FP32 sweeps, FP64 residual 1e-12).
+The check also prints the ratio to rel |d| + floor S_k, S_k = sum_i |c[i, k] y_i| (the size of
+the pole terms before they cancel), as a diagnostic of how close a channel is to the
+cancellation limit of FP64 arithmetic.
 """
 import numpy as np
 import pytest
