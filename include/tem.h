@@ -335,7 +335,9 @@ int tem_server_destroy(tem_server* srv);
  *     in device memory that the library defines statically, instead of a per-call buffer;
  *   - the grid's device must be the current device (TEM_EINVAL otherwise);
  *   - the first call on a device looks up that array's device address once
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *     (cudaGetSymbolAddress) and keeps it for the life of the process: it assumes the
+ *     runtime's primary context of that device and no cudaDeviceReset in between; make that
+ *     first call before any stream capture;
  *   - every call shares the array and leaves its shifts there; calls whose work
  *     overlaps on the GPU (for example on two streams at once) race on it.
  * Enqueued on cuda_stream; returns without synchronising.  Allocates nothing.

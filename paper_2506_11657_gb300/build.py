@@ -40,8 +40,16 @@ def _compile(src, nvcc, extra):
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
+def build(verbose: bool = False, extra=(), out=None, build_dir=None) -> str:
     """Compile and link; returns the library path.  Rebuilds only when a source is newer."""
+    global BUILD, OUT
+    if out is not None or build_dir is not None:
+        saved = (BUILD, OUT)
+        BUILD, OUT = build_dir or BUILD, out or OUT
+        try:
+            return build(verbose, extra)
+        finally:
+            BUILD, OUT = saved
     os.makedirs(BUILD, exist_ok=True)
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(HERE, "..", "include", "tem.h")]
@@ -59,6 +67,14 @@ def build(verbose: bool = False, extra=()) -> str:
     if verbose:
         print("built", OUT, file=sys.stderr)
     return OUT
+
+
+def build_checked(verbose: bool = False) -> str:
+    """The bounds-checked variant (-DTEM_CHECK_BOUNDS: every global index and TMA box start of the
+    hot kernels is checked; a failing check is recorded and reported instead of faulting) as
+    libtem_checked.so next to libtem.so.  Select it at run time with TEM_LIB=<path>."""
+    return build(verbose, extra=("-DTEM_CHECK_BOUNDS",), out=os.path.join(HERE, "libtem_checked.so"),
+                 build_dir=os.path.join(HERE, "_build_checked"))
 
 
 if __name__ == "__main__":

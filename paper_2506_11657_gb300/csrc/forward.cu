@@ -98,6 +98,7 @@ extern "C" {
 int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop, double current,
                 const double* rx_xyz, int64_t n_rx, const double* xi, const double* c, int64_t s, int64_t K,
                 const tem_options* opt_in, void* cuda_stream, double* dbzdt_out, tem_state** state_out) {
+  NvtxRange range("tem_forward");
   if (!grid || !dbzdt_out || !rx_xyz || n_rx < 1 || n_rx > 4096) return TEM_EINVAL;
   if (state_out) *state_out = nullptr;
   tem_options opt;
@@ -330,6 +331,7 @@ int tem_state_fields(const tem_state* state, int64_t k0, int64_t nk, void* cuda_
 }
 
 int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) {
+  NvtxRange range("tem_adjoint");
   if (!S || !g || !grad || !S->batch) return TEM_EINVAL;
   if (S->grid->sigma_gen != S->sigma_gen) {
     set_last_error("tem_adjoint: the grid's conductivity changed after the forward call", __FILE__, __LINE__);
@@ -413,6 +415,7 @@ int tem_adjoint(tem_state* S, const double* g, void* cuda_stream, double* grad) 
 }
 
 int tem_jvp(tem_state* S, const double* dlogsigma, void* cuda_stream, double* ddbzdt_out) {
+  NvtxRange range("tem_jvp");
   if (!S || !dlogsigma || !ddbzdt_out || !S->batch) return TEM_EINVAL;
   if (S->grid->sigma_gen != S->sigma_gen) {
     set_last_error("tem_jvp: the grid's conductivity changed after the forward call", __FILE__, __LINE__);

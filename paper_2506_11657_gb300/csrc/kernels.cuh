@@ -27,6 +27,33 @@
 
 namespace tem {
 
+// ---------------------------------------------------------------- bounds-checked build
+// Built with -DTEM_CHECK_BOUNDS, the hot kernels check every global index (and the alignment of
+// every TMA box) before the access.  A failing check records the first (site, index) in a
+// device word and skips the access instead of faulting; Batch::solve and the server report it.
+// Without the macro every check is the constant true and compiles away.
+#ifdef TEM_CHECK_BOUNDS
+static __device__ unsigned long long g_tem_fault = 0ull;
+__device__ __forceinline__ bool index_ok(int64_t idx, int64_t n, int site) {
+  if (idx >= 0 && idx < n) return true;
+  atomicCAS(&g_tem_fault, 0ull, ((unsigned long long)site << 48) | ((unsigned long long)idx & 0xffffffffffffull));
+  return false;
+}
+#define TEM_CHECK(idx, n, site) ::tem::index_ok((int64_t)(idx), (int64_t)(n), (site))
+// Read and clear the record (0: no failed check); host side, synchronises the stream.
+static inline unsigned long long take_bounds_fault(cudaStream_t st) {
+  unsigned long long v = 0ull;
+  const unsigned long long z = 0ull;
+  cudaMemcpyFromSymbolAsync(&v, g_tem_fault, sizeof(v), 0, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyToSymbolAsync(g_tem_fault, &z, sizeof(z), 0, cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  return v;
+}
+#else
+#define TEM_CHECK(idx, n, site) true
+static inline unsigned long long take_bounds_fault(cudaStream_t) { return 0ull; }
+#endif
+
 // ---------------------------------------------------------------- complex
 template <class T> struct C2 {
   T re, im;
@@ -662,8 +689,11 @@ __device__ __forceinline__ void pipe_form(pipe::Smem& sm, const PipePos& pp, int
       v.y += beta.re * o.y + beta.im * o.x;
       sm.P[b][c][r] = v;
       if (own) {
-        if (c < 3) anew[c * nc + n] = v;
-        else if (bnew) bnew[n] = v;
+        if (c < 3) {
+          if (TEM_CHECK(c * nc + n, 3 * nc, 1)) anew[c * nc + n] = v;
+        } else if (bnew && TEM_CHECK(n, nc, 2)) {
+          bnew[n] = v;
+        }
       }
     }
   }
@@ -832,7 +862,7 @@ static __global__ void __launch_bounds__(NT, TEM_PIPE_MIN_CTAS) k_cocg_stencil_p
           acc.re += pc[c].x * qv.x - pc[c].y * qv.y;
           acc.im += pc[c].x * qv.y + pc[c].y * qv.x;
         }
-        q[c * nc + n] = qv;
+        if (TEM_CHECK(c * nc + n, 3 * nc, 3)) q[c * nc + n] = qv;
       }
       if (interior && pa.nodal) {
         // (G^T M p)_n: +M p / L on the arriving edges, -M p / L on the leaving ones
@@ -847,7 +877,7 @@ static __global__ void __launch_bounds__(NT, TEM_PIPE_MIN_CTAS) k_cocg_stencil_p
         float2 v;
         v.x = cx * pxm.x + cy * pym.x + cz * pzm.x - ox * pc[0].x - oy * pc[1].x - oz * pc[2].x;
         v.y = cx * pxm.y + cy * pym.y + cz * pzm.y - ox * pc[0].y - oy * pc[1].y - oz * pc[2].y;
-        gpo[n] = v;
+        if (TEM_CHECK(n, nc, 4)) gpo[n] = v;
       }
       fxm = fx;
       fym = fy;
@@ -994,6 +1024,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
   const int64_t n = ne + (d.nodal ? g.ncomp : 0);
   const int64_t per = (n + d.nblk_update - 1) / d.nblk_update;
   const int64_t e0 = (int64_t)lb * per, e1 = min(n, e0 + per);
+  if (e1 > e0 && !TEM_CHECK(e1 - 1, n, 11)) return;
   C2<T> rz = czero<T>();
   T rr = T(0);
   const int64_t ee = min(e1, ne);
@@ -1118,6 +1149,7 @@ static __global__ void __launch_bounds__(NT, 3) k_cocg_update_vec(BatchArgs A) {
   const int64_t ne2 = 3 * nc / 2, n2 = ne2 + (d.nodal ? nc / 2 : 0);
   const int64_t per = (n2 + d.nblk_update - 1) / d.nblk_update;
   const int64_t p0 = (int64_t)lb * per, p1 = min(n2, p0 + per);
+  if (p1 > p0 && !TEM_CHECK(p1 - 1, n2, 12)) return;
   C2<float> rz = czero<float>(), rn = czero<float>();
   float rr = 0.f;
   constexpr int U = 2;
@@ -1354,12 +1386,14 @@ struct ResidualPol {
     rr += r.re * r.re + r.im * r.im;
     const C2<TI> rs(TI(scale * r.re), TI(scale * r.im));
     const C2<TI> wv = cdiv(rs, jacobi_D<TI>(GI, c, i, j, k, idx, C2<TI>(xr, xim)));
-    st<TI>(win, idx, wv);
+    if (TEM_CHECK(idx, 3 * g->ncomp, 5)) st<TI>(win, idx, wv);
     const C2<TI> pz = cmul(rs, wv);
     rz_re += double(pz.re);
     rz_im += double(pz.im);
   }
-  __device__ void edge_invalid(int64_t idx) { st<TI>(win, idx, czero<TI>()); }
+  __device__ void edge_invalid(int64_t idx) {
+    if (TEM_CHECK(idx, 3 * g->ncomp, 6)) st<TI>(win, idx, czero<TI>());
+  }
 };
 
 template <class TI>

@@ -10,6 +10,7 @@
 //               to x in FP64 and recomputes r in FP64 (defect correction).
 #include <algorithm>
 #include <atomic>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -372,10 +373,20 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
   auto poll = [&]() -> int {
     TEM_CUDA_TRY(cudaMemcpyAsync(counters_h_, counters_d_.ptr, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     TEM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (const unsigned long long f = take_bounds_fault(st)) {   // only in the bounds-checked build
+      char msg[128];
+      snprintf(msg, sizeof(msg), "bounds check failed: site %llu, index %llu", f >> 48, f & 0xffffffffffffull);
+      set_last_error(msg, __FILE__, __LINE__);
+      return TEM_ECUDA;
+    }
     return TEM_OK;
   };
-  TEM_TRY(launch_residual(st));
-  TEM_TRY(launch_nodal(st, 1));
+  NvtxRange range("tem: batched shifted COCG");
+  {
+    NvtxRange r("tem: FP64 residual + start");
+    TEM_TRY(launch_residual(st));
+    TEM_TRY(launch_nodal(st, 1));
+  }
   launches += 2;
   TEM_TRY(poll());
   int done_seen = 0;
@@ -388,6 +399,7 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
     }
     if (++rounds > max_rounds) return TEM_ETIMEOUT;
     if (counters_h_[0] > 0) {
+      NvtxRange r("tem: COCG iterations (stencil + update passes)");
       for (int it = 0; it < every; ++it) {
         TEM_TRY(launch_iteration(st));
         launches += launches_per_iteration();
@@ -395,6 +407,7 @@ int Batch::solve(const tem_options& opt, cudaStream_t st, SolveStats* stats) {
     }
     // slots whose inner solve ended take their FP64 outer step (the others skip it),
     // and the nodal pass starts the inner solves that step armed
+    NvtxRange r("tem: FP64 residual + start");
     TEM_TRY(launch_residual(st));
     TEM_TRY(launch_nodal(st, 1));
     launches += 2;

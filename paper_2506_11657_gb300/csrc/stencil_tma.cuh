@@ -132,6 +132,7 @@ __device__ __forceinline__ void issue_plane(const Ring& R, const CUtensorMap* ma
   if (use_beta) bytes += VEC_B + (nodal ? NOD_B : 0u);
   mbar_expect_tx(bar, bytes);
   const int x0 = 2 * (i0 - 2);   // float coordinate of column i0-2 (a multiple of 4: 16 bytes)
+  if (!TEM_CHECK(x0 & 3, 1, 7)) return;   // a misaligned box start: record it, issue nothing
   load4(R.vec(sw), maps + MAP_W, x0, j0 - 1, p, 0, bar);
   if (nodal) load3(R.nod(sw), maps + MAP_PSI, x0, j0 - 1, p, bar);
   load4(R.mass(sw), maps + MAP_MQ, 0, i0 - 2, j0 - 1, p, bar);
@@ -192,7 +193,7 @@ __device__ __forceinline__ void form_plane(const Ring& R, int sw, int so, const 
       v.w += br * o.w + bi * o.z;
       W[off] = v;
     }
-    if (st) ga[c < 3 ? c * nc4 : 0] = v;
+    if (st && TEM_CHECK(plane4 + f.g + (c < 3 ? c * nc4 : 0), c < 3 ? 3 * nc4 : nc4, 8)) ga[c < 3 ? c * nc4 : 0] = v;
   }
 }
 
@@ -389,7 +390,7 @@ __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
         accr += pc[c].x * qv.x - pc[c].y * qv.y;
         acci += pc[c].x * qv.y + pc[c].y * qv.x;
       }
-      qk[c * nc] = qv;
+      if (TEM_CHECK(i + (int64_t)nx * j + sxy * k + c * nc, 3 * nc, 9)) qk[c * nc] = qv;
     }
     if (nodal && i > 0 && j > 0 && k > 0) {
       // (G^T M p)_n: +M p / L on the three arriving edges, -M p / L on the three leaving ones
@@ -404,7 +405,7 @@ __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
       float2 v;
       v.x = cx * pxm.x + cy * pym.x + cz * pzm.x - ox * pc[0].x - oy * pc[1].x - oz * pc[2].x;
       v.y = cx * pxm.y + cy * pym.y + cz * pzm.y - ox * pc[0].y - oy * pc[1].y - oz * pc[2].y;
-      *gk = v;
+      if (TEM_CHECK(i + (int64_t)nx * j + sxy * k, nc, 10)) *gk = v;
     }
     fxm = fx;
     fym = fy;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cstdint>
 #include <cstddef>
 #include <vector>
@@ -34,6 +35,15 @@ struct Status {
   } while (0)
 
 void set_last_error(const char* msg, const char* file, int line);
+
+// A named NVTX range for the lifetime of the object (visible in Nsight timelines; no cost
+// without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---- device memory ---------------------------------------------------------
 void* dev_alloc(size_t bytes, cudaStream_t stream);

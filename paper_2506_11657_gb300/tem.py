@@ -2,7 +2,10 @@
 
 Argument marshalling only: every step of the forward model, the adjoint and
 the operator runs in libtem.so's CUDA kernels.  PyTorch supplies device memory
-(through the allocator hook) and streams.  Loading fails loudly if the library
+and streams: when torch has CUDA, loading the library installs PyTorch's caching
+allocator as the library's allocator (tem_set_allocator), so every device buffer the
+library creates is a torch allocation on the caller's stream (TEM_ALLOCATOR=cuda keeps
+the library's own stream-ordered pool instead).  Loading fails loudly if the library
 has not been built; there is no CPU fallback.
 """
 from __future__ import annotations
@@ -14,7 +17,7 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libtem.so")
+LIB_PATH = os.environ.get("TEM_LIB") or os.path.join(HERE, "libtem.so")   # TEM_LIB: another build of it
 
 TEM_OK, TEM_EINVAL, TEM_ENOMEM, TEM_ENOCONV, TEM_EBREAKDOWN, TEM_ETIMEOUT, TEM_ECUDA, TEM_EBUSY = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
@@ -104,8 +107,58 @@ def lib():
     L.tem_launch_count.restype = C.c_int64
     L.tem_profile_passes.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, C.c_int32,
                                      C.c_int32, C.c_int32, C.c_void_p, _dp, _dp]
+    L.tem_set_allocator.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
     _lib = L
+    _install_torch_allocator(L)
     return L
+
+
+# ---- device memory from PyTorch's caching allocator (tem_set_allocator)
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_allocator = "cuda"
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), int(stream or 0))
+    except Exception:
+        return None                       # NULL: the library reports TEM_ENOMEM
+
+
+def _torch_free(ptr, nbytes, stream, ctx):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:
+        pass
+
+
+_alloc_cb = _ALLOC_FN(_torch_alloc)       # kept alive for the life of the process
+_free_cb = _FREE_FN(_torch_free)
+
+
+def _install_torch_allocator(L):
+    global _allocator
+    if os.environ.get("TEM_ALLOCATOR", "torch") != "torch":
+        return
+    try:
+        import torch
+        if not torch.cuda.is_available():
+            return
+    except ImportError:
+        return
+    rc = L.tem_set_allocator(C.cast(_alloc_cb, C.c_void_p), C.cast(_free_cb, C.c_void_p), None)
+    if rc == TEM_OK:
+        _allocator = "torch"
+
+
+def allocator():
+    """Which allocator the library uses: "torch" (PyTorch's caching allocator) or "cuda" (its own
+    cudaMallocAsync pool)."""
+    lib()
+    return _allocator
 
 
 def status_string(code):
