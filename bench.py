@@ -320,6 +320,34 @@ def run_derivatives(stream, dev):
             "transpose_rel_gap": abs(lhs - rhs) / (np.sum(np.abs(gres * jd)) + np.sum(np.abs(gr * dm)))}
 
 
+def run_single_time(stream):
+    """Sec. 3.1's single-time baseline against the shared-pole family on the 64^3 random-block model
+    (31 channels): the single-time approximant of degree 14 (7 shifts, 217 solves: each channel its
+    own) and the shared-pole family of degree 20 (10 solves for all channels), both mixed precision
+    to an FP64 residual of 1e-12, timed with CUDA events; and how far their responses differ."""
+    import torch
+    from paper_2506_11657_gb300 import tem, workloads as W
+    m = W.randblock128(n=64)
+    g = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma, stream=stream)
+    opt = tem.default_options(precision="mixed", tol=1e-12)
+    xi1, c1, err1 = tem.poles_residues([1.0], 14)
+    sh, c, err = tem.poles_residues(m.t, m.degree)
+    tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, opt, stream=stream)     # warm
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    d_shared = tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, opt, stream=stream).d
+    e[1].record(stream)
+    d_single, solves = tem.forward_single_time(g, m.loop_xy, m.z_loop, m.rx, m.t, xi1, c1[:, 0], opt, stream=stream)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    g.close()
+    rel = np.abs(d_single - d_shared) / np.abs(d_shared)
+    return {"workload": "randblock64", "channels": len(m.t),
+            "shared_poles": {"degree": m.degree, "solves": len(sh), "uniform_err": err, "ms": e[0].elapsed_time(e[1])},
+            "single_time": {"degree": 14, "solves": solves, "uniform_err": err1, "ms": e[1].elapsed_time(e[2])},
+            "max_rel_diff": float(rel.max()), "median_rel_diff": float(np.median(rel))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,6 +361,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=16)
     ap.add_argument("--serving-only", action="store_true")
     ap.add_argument("--no-derivatives", action="store_true")
+    ap.add_argument("--no-single-time", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -438,6 +467,7 @@ def main():
         fbytes = 3 * model.sigma.size * (16 * len(shifts) + 8 * len(model.t))
         snaps = {"ms_all_channels": fms, "gbs": fbytes / (fms * 1e-3) / 1e9}
     derivs = run_derivatives(stream, dev) if not args.no_derivatives else None
+    single = run_single_time(stream) if not args.no_single_time else None
 
     # per-launch timing of the passes with all shifts active (CUDA events on the launching stream)
     prof = tem.profile_passes(grid, model.loop_xy, model.z_loop, shifts, tem.PREC_MIXED, n_iter=20, stream=stream)
@@ -507,7 +537,7 @@ def main():
                 "iters_per_shift_mixed": iters_mixed.tolist(), "relres_mixed": relres_mixed.tolist(),
                 "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(n1 - n0), "clocks": clocks, "serving": serving,
-                "derivatives": derivs, "field_snapshots": snaps}
+                "derivatives": derivs, "field_snapshots": snaps, "single_time_baseline": single}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

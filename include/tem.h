@@ -205,6 +205,23 @@ int tem_forward_sources(const tem_grid* grid, const double* loops_xy, const int6
                         void* cuda_stream, double* dbzdt_out);
 
 /*
+ * The single-time best-approximation baseline (Sec. 3.1, Eq. (rba)), the comparison method of the
+ * paper: one rational approximant r(x) = sum_i Re(c_i / (x - xi_i)) ~= exp(-x) on x >= 0 (xi, c as
+ * returned by tem_poles_residues for the single time t = 1, so s shifts and one channel) is
+ * evaluated at every channel t_k separately:
+ *   d[r, k] = sum_i Re( c_i q_r^T (t_k K - xi_i M)^{-1} f )
+ *           = sum_i Re( (c_i / t_k) q_r^T (K - (xi_i / t_k) M)^{-1} f ),
+ * i.e. K * s shifted solves instead of the s of tem_forward's shared poles; they run through the
+ * same batched solver, 64 shifts at a time.  t: K channel times (s), finite and > 0.  Other
+ * arguments, the output layout and the statuses as for tem_forward (opt->keep_state is ignored).
+ * solves_out (may be NULL) receives K * s.
+ */
+int tem_forward_single_time(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop,
+                            double current, const double* rx_xyz, int64_t n_rx, const double* t, int64_t K,
+                            const double* xi, const double* c, int64_t s, const tem_options* opt,
+                            void* cuda_stream, double* dbzdt_out, int64_t* solves_out);
+
+/*
  * Per-shift diagnostics of the last forward (or adjoint) solve kept in `state`:
  *   iters[s]   : COCG iterations (inner FP32 iterations summed, for MIXED),
  *   relres[s]  : final FP64 relative residual ||f - A_i x_i|| / ||f||.

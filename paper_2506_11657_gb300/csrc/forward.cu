@@ -4,6 +4,7 @@
 // Adjoint (Sec. 4):      grad[c] = sum_i Re(xi_i lambda_i^T (dM/dlog sigma_c) x_i),
 //                        lambda_i = (K - xi_i M)^{-1} sum_r beta[i, r] q_r,
 //                        beta[i, r] = sum_k c[i, k] g[r, k].
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -602,3 +603,43 @@ int tem_profile_passes(const tem_grid* grid, const double* loop_xy, int64_t n_ve
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ the single-time baseline (Sec. 3.1)
+extern "C" int tem_forward_single_time(const tem_grid* grid, const double* loop_xy, int64_t n_vertices, double z_loop,
+                                       double current, const double* rx_xyz, int64_t n_rx, const double* t, int64_t K,
+                                       const double* xi, const double* c, int64_t s, const tem_options* opt_in,
+                                       void* cuda_stream, double* dbzdt_out, int64_t* solves_out) {
+  NvtxRange range("tem_forward_single_time");
+  if (!grid || !t || !dbzdt_out || !rx_xyz || K < 1 || K > 100000 || n_rx < 1 || n_rx > 4096) return TEM_EINVAL;
+  TEM_TRY(validate_poles(xi, c, s, 1));
+  for (int64_t k = 0; k < K; ++k)
+    if (!(std::isfinite(t[k]) && t[k] > 0.0)) return TEM_EINVAL;
+  tem_options opt;
+  tem_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  opt.keep_state = 0;
+  // channel k takes its own s systems (t_k K - xi_i M) x = f, i.e. the shifts xi_i / t_k with
+  // the weights c_i / t_k on channel k alone; they go through the batched solver 64 at a time
+  const int64_t total = s * K;
+  std::vector<double> sum((size_t)n_rx * K, 0.0), part((size_t)n_rx * K);
+  int worst = TEM_OK;
+  for (int64_t j0 = 0; j0 < total; j0 += 64) {
+    const int64_t ns = std::min<int64_t>(64, total - j0);
+    std::vector<double> xs(2 * ns), cs(2 * ns * K, 0.0);
+    for (int64_t j = 0; j < ns; ++j) {
+      const int64_t q = j0 + j, k = q / s, i = q % s;
+      xs[2 * j] = xi[2 * i] / t[k];
+      xs[2 * j + 1] = xi[2 * i + 1] / t[k];
+      cs[2 * (j * K + k)] = c[2 * i] / t[k];
+      cs[2 * (j * K + k) + 1] = c[2 * i + 1] / t[k];
+    }
+    const int rc = tem_forward(grid, loop_xy, n_vertices, z_loop, current, rx_xyz, n_rx, xs.data(), cs.data(), ns, K,
+                               &opt, cuda_stream, part.data(), nullptr);
+    if (rc != TEM_OK && rc != TEM_ENOCONV) return rc;
+    if (rc == TEM_ENOCONV) worst = TEM_ENOCONV;
+    for (size_t q = 0; q < sum.size(); ++q) sum[q] += part[q];
+  }
+  std::memcpy(dbzdt_out, sum.data(), sum.size() * sizeof(double));
+  if (solves_out) *solves_out = total;
+  return worst;
+}

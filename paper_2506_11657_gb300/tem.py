@@ -25,7 +25,7 @@ PRECOND_AUTO, PRECOND_JACOBI, PRECOND_NODAL = 0, 1, 2
 
 EXPORTED = ["tem_default_options", "tem_status_string", "tem_version", "tem_set_allocator",
             "tem_build_grid", "tem_grid_set_sigma", "tem_grid_dims", "tem_grid_destroy",
-            "tem_poles_residues", "tem_forward", "tem_forward_sources", "tem_state_stats", "tem_state_solution", "tem_state_fields", "tem_adjoint", "tem_jvp",
+            "tem_poles_residues", "tem_forward", "tem_forward_sources", "tem_forward_single_time", "tem_state_stats", "tem_state_solution", "tem_state_fields", "tem_adjoint", "tem_jvp",
             "tem_state_destroy", "tem_apply_operator", "tem_apply_operator_noalloc", "tem_launch_count",
             "tem_profile_passes", "tem_server_default_options", "tem_server_create", "tem_server_submit",
             "tem_server_step", "tem_server_poll", "tem_server_counts", "tem_server_destroy"]
@@ -85,6 +85,8 @@ def lib():
     L.tem_state_stats.argtypes = [C.c_void_p, _i32p, _dp]
     L.tem_forward_sources.argtypes = [C.c_void_p, _dp, _i64p, C.c_int64, _dp, _dp, _dp, C.c_int64, _dp, _dp,
                                       C.c_int64, C.c_int64, C.POINTER(Options), C.c_void_p, _dp]
+    L.tem_forward_single_time.argtypes = [C.c_void_p, _dp, C.c_int64, C.c_double, C.c_double, _dp, C.c_int64, _dp,
+                                          C.c_int64, _dp, _dp, C.c_int64, C.POINTER(Options), C.c_void_p, _dp, _i64p]
     L.tem_state_solution.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, _dp]
     L.tem_state_fields.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p]
     L.tem_adjoint.argtypes = [C.c_void_p, _dp, C.c_void_p, _dp]
@@ -369,6 +371,27 @@ def forward_sources(grid: Grid, loops, z_loops, rx, shifts, c, options: Options 
                                    s, K, C.byref(opt), _stream(stream), _ptr(out))
     _check(rc, "tem_forward_sources", ok=(TEM_OK, TEM_ENOCONV))
     return out
+
+
+def forward_single_time(grid: Grid, loop_xy, z_loop, rx, t, shifts, c, options: Options | None = None, current=1.0,
+                        stream=None):
+    """tem_forward_single_time: the single-time baseline of Sec. 3.1.  shifts, c: the fit of
+    exp(-x) for t = 1 (poles_residues([1.0], m)); t: the K channel times.  Returns (d (n_rx, K),
+    number of shifted solves)."""
+    loop = _f64(loop_xy).reshape(-1, 2)
+    rxa = _f64(rx).reshape(-1, 3)
+    tt = _f64(t)
+    shifts = np.ascontiguousarray(shifts, dtype=np.complex128)
+    cc = np.ascontiguousarray(np.asarray(c).reshape(len(shifts)), dtype=np.complex128)
+    opt = options or default_options()
+    out = np.zeros((len(rxa), len(tt)))
+    solves = C.c_int64()
+    rc = lib().tem_forward_single_time(grid.handle, _ptr(loop), len(loop), float(z_loop), float(current), _ptr(rxa),
+                                       len(rxa), _ptr(tt), len(tt), _ptr(shifts.view(np.float64)),
+                                       _ptr(cc.view(np.float64)), len(shifts), C.byref(opt), _stream(stream), _ptr(out),
+                                       C.byref(solves))
+    _check(rc, "tem_forward_single_time", ok=(TEM_OK, TEM_ENOCONV))
+    return out, int(solves.value)
 
 
 def apply_operator(grid: Grid, shifts, p, q, precision=PREC_FP64, stream=None):

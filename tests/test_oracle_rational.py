@@ -135,3 +135,35 @@ def test_physical_scaling():
     lam = np.logspace(1, 7, 50)
     approx = ((1.0 / (lam[:, None] - sh[None, :])) @ c).real
     assert np.abs(approx - np.exp(-np.outer(lam, t))).max() <= 1.01 * err + 1e-15
+
+
+# Halphen's constant, the geometric rate of the best rational approximation to exp(-x) on
+# [0, inf): error ~ 2 H^(-m-1/2) (Sec. 3.3, citing Trefethen, Approximation Theory and Practice).
+HALPHEN = 9.289025491920819
+
+
+def test_single_time_fit_follows_halphen():
+    """The single-time approximant of Sec. 3.1 (the fitter on the one time t = 1, type [(m-1)/m]):
+    for m = 3..10 its uniform error on [0, inf) lies between half and three times Halphen's
+    2 H^(-m-1/2) (the best type-[m/m] error, which no approximant of this type can beat by more
+    than the formula's asymptotic slack), falls by a factor H per degree on average, and it reaches
+    each accuracy of the paper's Table (ratio-1 column: the classical best approximation) at
+    that degree or one more."""
+    errs = {}
+    for m in range(2, 13):
+        _, _, errs[m] = R.tem_poles_residues([1.0], m)
+    for m in range(3, 11):
+        h = 2.0 * HALPHEN ** (-m - 0.5)
+        assert 0.5 * h <= errs[m] <= 3.0 * h, (m, errs[m], h)
+    rate = np.exp(np.mean([np.log(errs[m] / errs[m + 1]) for m in range(3, 10)]))
+    assert 7.5 <= rate <= 11.5, rate
+    table = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "degree_table.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = line.split()
+            table[float(v[0])] = int(v[1])
+    for acc, m_best in table.items():
+        m_ours = min(m for m in errs if errs[m] <= acc)
+        assert m_best <= m_ours <= m_best + 1, (acc, m_best, m_ours)
