@@ -57,9 +57,9 @@ def pass_bytes(s):
         "kernel": {
             # edges w, a_old read, a, q written; nodes psi, b_old read, b, G^T M p written; masses
             "stencil": 32.0 + 4 * NODE + (16.0 / 3.0) / s,
-            # edges x, a, w, q read, x, w written; diag K, M_e; nodes x_n, b, u, G^T M p, c_n read,
-            # x_n, u, psi written; W_n
-            "update": 48.0 + 8.0 / s + 8 * NODE + (4.0 / 3.0) / s,
+            # edges x, a, w, q read, x, w written; diag K, M_e; nodes x_n, b, v, G^T M p read,
+            # x_n, v, psi written; W_n
+            "update": 48.0 + 8.0 / s + 7 * NODE + (4.0 / 3.0) / s,
         },
     }
 
@@ -348,6 +348,38 @@ def run_single_time(stream):
             "max_rel_diff": float(rel.max()), "median_rel_diff": float(np.median(rel))}
 
 
+def run_sources(stream, n_src=4):
+    """Several loop sources (block f, Sec. 4) on the 64^3 model: n_src loops of 120-280 m solved as
+    one batch of n_src x 10 shifted systems (tem_forward_sources) against n_src separate forwards,
+    mixed precision to 1e-12, CUDA events; the batch reads the per-grid arrays once per tile for
+    all systems."""
+    import torch
+    from paper_2506_11657_gb300 import tem, workloads as W
+    m = W.randblock128(n=64)
+    g = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma, stream=stream)
+    opt = tem.default_options(precision="mixed", tol=1e-12)
+    sh, c, _ = tem.poles_residues(m.t, m.degree)
+    xn = m.origin[0] + np.concatenate(([0.0], np.cumsum(m.hx)))
+    loops = []
+    for side in np.linspace(120.0, 280.0, n_src):
+        a = xn[np.argmin(np.abs(xn + side / 2))]
+        b = xn[np.argmin(np.abs(xn - side / 2))]
+        loops.append(np.array([[a, a], [b, a], [b, b], [a, b]]))
+    tem.forward(g, loops[0], 0.0, m.rx, sh, c, opt, stream=stream)      # warm
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record(stream)
+    D = tem.forward_sources(g, loops, 0.0, m.rx, sh, c, opt, stream=stream)
+    e[1].record(stream)
+    sep = [tem.forward(g, lp, 0.0, m.rx, sh, c, opt, stream=stream).d for lp in loops]
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    g.close()
+    same = all(np.array_equal(D[j], sep[j]) for j in range(n_src))
+    return {"workload": "randblock64", "sources": n_src, "systems_per_batch": n_src * len(sh),
+            "batched_ms": e[0].elapsed_time(e[1]), "separate_ms": e[1].elapsed_time(e[2]),
+            "bitwise_equal_to_separate": bool(same)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -468,6 +500,7 @@ def main():
         snaps = {"ms_all_channels": fms, "gbs": fbytes / (fms * 1e-3) / 1e9}
     derivs = run_derivatives(stream, dev) if not args.no_derivatives else None
     single = run_single_time(stream) if not args.no_single_time else None
+    sources = run_sources(stream) if not args.no_single_time else None
 
     # per-launch timing of the passes with all shifts active (CUDA events on the launching stream)
     prof = tem.profile_passes(grid, model.loop_xy, model.z_loop, shifts, tem.PREC_MIXED, n_iter=20, stream=stream)
@@ -537,7 +570,8 @@ def main():
                 "iters_per_shift_mixed": iters_mixed.tolist(), "relres_mixed": relres_mixed.tolist(),
                 "fp64": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(n1 - n0), "clocks": clocks, "serving": serving,
-                "derivatives": derivs, "field_snapshots": snaps, "single_time_baseline": single}
+                "derivatives": derivs, "field_snapshots": snaps, "single_time_baseline": single,
+                "multiple_sources": sources}
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -1063,7 +1063,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
       rr += r.re * r.re + r.im * r.im;
     }
   }
-  // nodal part: x_n += alpha b;  u = G^T M d += alpha G^T M p;  psi = (cn + xi u) / D_n
+  // nodal part: x_n += alpha b;  v = cn + xi G^T M d += alpha xi G^T M p;  psi = v / D_n
+  // (v is kept in the u buffer: the start pass sets it to cn, so cn is not read here)
   const T* __restrict__ Wn = Geo<T>(g).Wn;
   C2<T> rn = czero<T>();
   for (int64_t e = max(e0, ne) + threadIdx.x; e < e1; e += NT) {
@@ -1073,10 +1074,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
     st<T>(d.xn, m, xn);
     const T wn = __ldg(Wn + m);
     if (wn == T(0)) continue;  // boundary node
-    C2<T> uv = cmul(alpha, ld<T>(d.gp, m));
-    if (!first) uv = uv + ld<T>(d.u, m);
-    st<T>(d.u, m, uv);
-    const C2<T> dv = ld<T>(d.cn, m) + cmul(xi, uv);
+    const C2<T> dv = ld<T>(d.u, m) + cmul(alpha, cmul(xi, ld<T>(d.gp, m)));
+    st<T>(d.u, m, dv);
     const C2<T> ps = cdiv(dv, wn * C2<T>(-xi.re, -xi.im));
     st<T>(d.psi, m, ps);
     rn = rn + cmul(dv, ps);
@@ -1112,15 +1111,17 @@ __device__ __forceinline__ void update_edge(float& x_re, float& x_im, float& w_r
   rr += r.re * r.re + r.im * r.im;
 }
 
-__device__ __forceinline__ void update_node(float& xn_re, float& xn_im, float& u_re, float& u_im, float& ps_re,
-                                            float& ps_im, float b_re, float b_im, float gp_re, float gp_im, float cn_re,
-                                            float cn_im, float wn, C2<float> alpha, C2<float> xi, C2<float>& rn) {
+// v = cn + xi G^T M d (kept in the u buffer; the start pass sets it to cn): v += alpha xi G^T M p
+__device__ __forceinline__ void update_node(float& xn_re, float& xn_im, float& v_re, float& v_im, float& ps_re,
+                                            float& ps_im, float b_re, float b_im, float gp_re, float gp_im, float wn,
+                                            C2<float> alpha, C2<float> xi, C2<float>& rn) {
   xn_re += alpha.re * b_re - alpha.im * b_im;
   xn_im += alpha.re * b_im + alpha.im * b_re;
-  if (wn == 0.f) return;   // boundary node: u and psi stay 0
-  u_re += alpha.re * gp_re - alpha.im * gp_im;
-  u_im += alpha.re * gp_im + alpha.im * gp_re;
-  const C2<float> dv = C2<float>(cn_re, cn_im) + cmul(xi, C2<float>(u_re, u_im));
+  if (wn == 0.f) return;   // boundary node: v and psi stay 0
+  const C2<float> ag = cmul(alpha, cmul(xi, C2<float>(gp_re, gp_im)));
+  v_re += ag.re;
+  v_im += ag.im;
+  const C2<float> dv(v_re, v_im);
   const C2<float> ps = cdiv(dv, wn * C2<float>(-xi.re, -xi.im));
   ps_re = ps.re;
   ps_im = ps.im;
@@ -1182,15 +1183,14 @@ static __global__ void __launch_bounds__(NT, 3) k_cocg_update_vec(BatchArgs A) {
       wv[p] = wr[u];
     }
   }
-  // nodal pairs: x_n += alpha b;  u = G^T M d += alpha G^T M p;  psi = (cn + xi u) / D_n
+  // nodal pairs: x_n += alpha b;  v = cn + xi G^T M d += alpha xi G^T M p;  psi = v / D_n
   const float4* __restrict__ gpv = static_cast<const float4*>(d.gp);
-  const float4* __restrict__ cnv = static_cast<const float4*>(d.cn);
   float4* __restrict__ xnv = static_cast<float4*>(d.xn);
   float4* __restrict__ uv = static_cast<float4*>(d.u);
   float4* __restrict__ psv = static_cast<float4*>(d.psi);
   for (int64_t base = max(p0, ne2) + threadIdx.x; base < p1; base += (int64_t)NT * U) {
     float2 wn[U];
-    float4 br[U], gr[U], cr[U], xr[U], ur[U];
+    float4 br[U], gr[U], xr[U], ur[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t m = base + (int64_t)u * NT - ne2;
@@ -1198,9 +1198,8 @@ static __global__ void __launch_bounds__(NT, 3) k_cocg_update_vec(BatchArgs A) {
         wn[u] = __ldg(Wn + m);
         br[u] = __ldg(bv + m);
         gr[u] = __ldg(gpv + m);
-        cr[u] = __ldg(cnv + m);
         xr[u] = first ? z4 : xnv[m];
-        ur[u] = first ? z4 : uv[m];
+        ur[u] = uv[m];
       }
     }
 #pragma unroll
@@ -1208,10 +1207,10 @@ static __global__ void __launch_bounds__(NT, 3) k_cocg_update_vec(BatchArgs A) {
       const int64_t m = base + (int64_t)u * NT - ne2;
       if (m + ne2 >= p1) continue;
       float4 pr = z4;
-      update_node(xr[u].x, xr[u].y, ur[u].x, ur[u].y, pr.x, pr.y, br[u].x, br[u].y, gr[u].x, gr[u].y, cr[u].x,
-                  cr[u].y, wn[u].x, alpha, xi, rn);
-      update_node(xr[u].z, xr[u].w, ur[u].z, ur[u].w, pr.z, pr.w, br[u].z, br[u].w, gr[u].z, gr[u].w, cr[u].z,
-                  cr[u].w, wn[u].y, alpha, xi, rn);
+      update_node(xr[u].x, xr[u].y, ur[u].x, ur[u].y, pr.x, pr.y, br[u].x, br[u].y, gr[u].x, gr[u].y, wn[u].x,
+                  alpha, xi, rn);
+      update_node(xr[u].z, xr[u].w, ur[u].z, ur[u].w, pr.z, pr.w, br[u].z, br[u].w, gr[u].z, gr[u].w, wn[u].y,
+                  alpha, xi, rn);
       xnv[m] = xr[u];
       uv[m] = ur[u];
       psv[m] = pr;
@@ -1318,6 +1317,7 @@ __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
         c0 = sc * c0;
         dv = C2<T>(T(c0.re), T(c0.im));
         st<T>(d.cn, n, dv);
+        st<T>(d.u, n, dv);   // v = cn + xi G^T M d with d = 0
       } else {
         dv = ld<T>(d.cn, n) + cmul(xi, div_Mv<T, T>(G, g, d.x, d.xn, i, j, int(k), n));
       }

@@ -151,7 +151,8 @@ struct SlotDesc {
   void* psi;                // D_n^{-1} G^T r
   void* b0; void* b1;       // nodal part of the search direction, double-buffered
   void* cn;                 // G^T of the inner right-hand side, s xi G^T M x64 (set when a solve starts)
-  void* u;                  // G^T M d, updated with the correction d (so G^T r = cn + xi u)
+  void* u;                  // v = cn + xi G^T M d: the start pass sets it to cn, the update pass adds
+                            // alpha xi G^T M p with the correction (so G^T r = v)
   void* gp;                 // G^T M p of the current direction, from the stencil pass
   int tiles_x, tiles_y, zchunks;  // stencil decomposition
   int zchunk;               // planes per stencil CTA (a function of this slot's grid only)
