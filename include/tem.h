@@ -178,7 +178,8 @@ int tem_poles_residues(const double* t, int64_t K, int64_t degree, const double*
  *   state_out  : if opt->keep_state, receives the kept solutions for
  *                tem_adjoint (release with tem_state_destroy); else may be NULL.
  * Returns TEM_ENOCONV (output written) if a shift hit max_iter,
- * TEM_EBREAKDOWN on a COCG breakdown, TEM_EINVAL on bad geometry.
+ * TEM_EBREAKDOWN on a COCG breakdown, TEM_EINVAL on bad geometry, TEM_ETIMEOUT if a bounded
+ * device-side wait of the FP32 stencil ran out (its slot stops; nothing hangs).
  */
 int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
                 double z_loop, double current, const double* rx_xyz, int64_t n_rx,
@@ -319,7 +320,7 @@ typedef struct tem_server_options {
 typedef struct tem_request_stats {
   double submit_s, admit_s, done_s;  /* host steady-clock times (s) */
   int64_t footprint_bytes;           /* device bytes the request held while running */
-  int32_t status;                    /* TEM_OK, TEM_ENOCONV or TEM_EBREAKDOWN */
+  int32_t status;                    /* TEM_OK, TEM_ENOCONV, TEM_EBREAKDOWN or TEM_ETIMEOUT */
   int32_t max_iters;                 /* largest per-shift COCG iteration count */
 } tem_request_stats;
 

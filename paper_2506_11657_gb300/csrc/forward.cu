@@ -86,7 +86,8 @@ int collect_status(const Batch& b, std::vector<int32_t>& iters, std::vector<doub
   for (const auto& S : b.scalars()) {
     iters.push_back(S.total_iters);
     relres.push_back(S.ff > 0 ? std::sqrt(S.rr64 / S.ff) : 0.0);
-    if (S.status == TEM_EBREAKDOWN) rc = TEM_EBREAKDOWN;
+    if (S.status == TEM_ETIMEOUT) rc = TEM_ETIMEOUT;   // a bounded device wait ran out
+    else if (S.status == TEM_EBREAKDOWN && rc != TEM_ETIMEOUT) rc = TEM_EBREAKDOWN;
     else if (S.status == TEM_ENOCONV && rc == TEM_OK) rc = TEM_ENOCONV;
   }
   return rc;
@@ -182,7 +183,7 @@ int tem_forward(const tem_grid* grid, const double* loop_xy, int64_t n_vertices,
   TEM_CUDA_TRY(cudaMemcpyAsync(dbzdt_out, d_out, n_rx * K * sizeof(double), cudaMemcpyDeviceToHost, st));
   TEM_CUDA_TRY(cudaStreamSynchronize(st));
   const int rc = collect_status(*S->batch, S->iters, S->relres);
-  if (rc == TEM_EBREAKDOWN) return rc;
+  if (rc == TEM_EBREAKDOWN || rc == TEM_ETIMEOUT) return rc;
   if (opt.keep_state) *state_out = S.release();
   else if (state_out) *state_out = nullptr;
   return rc;

@@ -301,7 +301,8 @@ struct tem_server {
     for (int i = 0; i < r.s; ++i) {
       const SlotScalars& S = sc_h[r.first_slot + i];
       r.max_iters = std::max(r.max_iters, (int)S.total_iters);
-      if (S.status == TEM_EBREAKDOWN) r.status = TEM_EBREAKDOWN;
+      if (S.status == TEM_ETIMEOUT) r.status = TEM_ETIMEOUT;
+      else if (S.status == TEM_EBREAKDOWN && r.status != TEM_ETIMEOUT) r.status = TEM_EBREAKDOWN;
       else if (S.status == TEM_ENOCONV && r.status == TEM_OK) r.status = TEM_ENOCONV;
       owner[r.first_slot + i] = -1;
     }
