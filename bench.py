@@ -186,7 +186,8 @@ def oracle_sample(name, steps, warmup, m):
     shifts, _, _ = R.tem_poles_residues(model.t, model.degree)
     S = T.Sampler(name, shifts)
     try:
-        setup = S.step(0)
+        # the solver set-up alone, twice (its time is subtracted from every sample)
+        setup = float(np.median([S.step(0) for _ in range(2)]))
         for _ in range(warmup):
             S.step(m)
         times = [S.step(m) for _ in range(steps)]
@@ -202,7 +203,7 @@ def cpu_baseline_leg():
     """The CPU baseline of the GPU arm: the 128^3 sample (scaled to a whole model by the oracle's
     own iteration counts) and one whole 32^3 model of the same family solved end to end."""
     from oracle import t2_counts as T
-    smp = oracle_sample("randblock128", steps=1, warmup=0, m=3)
+    smp = oracle_sample("randblock128", steps=2, warmup=0, m=8)
     if smp is None:
         return None
     whole = T.count("randblock32")
@@ -220,20 +221,20 @@ def cpu_baseline_leg():
 
 def run_reference(args):
     """--impl reference: the CPU oracle, as it stands, on the same workload and metric.  Each
-    step is a bounded sample (3 T2 iterations of every shift, one process per shift)."""
+    step is a bounded sample (8 T2 iterations of every shift, one process per shift)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     from paper_2506_11657_gb300 import workloads as W
     model = W.randblock128()
     t0 = time.perf_counter()
-    smp = oracle_sample("randblock128", steps=args.steps, warmup=args.warmup, m=3)
+    smp = oracle_sample("randblock128", steps=args.steps, warmup=args.warmup, m=8)
     wall = time.perf_counter() - t0
     if smp is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle/t2_counts_randblock128.json is missing"}))
         return
     value = 1.0 / smp["model_s"]
-    desc = (f"each step: 3 iterations of oracle T2 (Jacobi-COCG, FP64) on every shift of randblock128, "
+    desc = (f"each step: 8 iterations of oracle T2 (Jacobi-COCG, FP64) on every shift of randblock128, "
             f"{smp['processes']} processes (one per shift); value = 1 / (assembly {smp['assembly_s']:.1f} s + "
             f"set-up {smp['setup_s']:.1f} s + the oracle's own T2 counts per shift at the measured time "
             f"per iteration)")
@@ -323,29 +324,38 @@ def run_derivatives(stream, dev):
 def run_single_time(stream):
     """Sec. 3.1's single-time baseline against the shared-pole family on the 64^3 random-block model
     (31 channels): the single-time approximant of degree 14 (7 shifts, 217 solves: each channel its
-    own) and the shared-pole family of degree 20 (10 solves for all channels), both mixed precision
-    to an FP64 residual of 1e-12, timed with CUDA events; and how far their responses differ."""
+    own) and the shared-pole families of degree 20 (10 solves; the workload's) and 38 (19 solves;
+    the degree the paper finds on par with single-time degree 14, Sec. 5), all mixed precision to
+    an FP64 residual of 1e-12, timed with CUDA events; and how far each shared-pole response is from
+    the single-time one per channel (the approximation error of the shared family: its uniform
+    error is absolute, so the late channels, ~1e7 below the early ones, show it most)."""
     import torch
     from paper_2506_11657_gb300 import tem, workloads as W
     m = W.randblock128(n=64)
     g = tem.Grid(m.hx, m.hy, m.hz, m.origin, m.sigma, stream=stream)
     opt = tem.default_options(precision="mixed", tol=1e-12)
     xi1, c1, err1 = tem.poles_residues([1.0], 14)
-    sh, c, err = tem.poles_residues(m.t, m.degree)
-    tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, opt, stream=stream)     # warm
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    tem.forward(g, m.loop_xy, m.z_loop, m.rx, xi1, np.repeat(c1, len(m.t), 1), opt, stream=stream)   # warm
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     e[0].record(stream)
-    d_shared = tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, opt, stream=stream).d
-    e[1].record(stream)
     d_single, solves = tem.forward_single_time(g, m.loop_xy, m.z_loop, m.rx, m.t, xi1, c1[:, 0], opt, stream=stream)
-    e[2].record(stream)
+    e[1].record(stream)
     torch.cuda.synchronize()
+    out = {"workload": "randblock64", "channels": len(m.t),
+           "single_time": {"degree": 14, "solves": solves, "uniform_err": err1, "ms": e[0].elapsed_time(e[1])}}
+    for degree in (m.degree, 38):
+        sh, c, err = tem.poles_residues(m.t, degree)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d_shared = tem.forward(g, m.loop_xy, m.z_loop, m.rx, sh, c, opt, stream=stream).d
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rel = np.abs(d_shared - d_single) / np.abs(d_single)
+        out[f"shared_poles_{degree}"] = {"degree": degree, "solves": len(sh), "uniform_err": err,
+                                         "ms": e0.elapsed_time(e1), "max_rel_diff_vs_single_time": float(rel.max()),
+                                         "median_rel_diff_vs_single_time": float(np.median(rel))}
     g.close()
-    rel = np.abs(d_single - d_shared) / np.abs(d_shared)
-    return {"workload": "randblock64", "channels": len(m.t),
-            "shared_poles": {"degree": m.degree, "solves": len(sh), "uniform_err": err, "ms": e[0].elapsed_time(e[1])},
-            "single_time": {"degree": 14, "solves": solves, "uniform_err": err1, "ms": e[1].elapsed_time(e[2])},
-            "max_rel_diff": float(rel.max()), "median_rel_diff": float(np.median(rel))}
+    return out
 
 
 def run_sources(stream, n_src=4):
