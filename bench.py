@@ -57,9 +57,10 @@ def pass_bytes(s):
         "kernel": {
             # edges w, a_old read, a, q written; nodes psi, b_old read, b, G^T M p written; masses
             "stencil": 32.0 + 4 * NODE + (16.0 / 3.0) / s,
-            # edges x, a, w, q read, x, w written; diag K, M_e; nodes x_n, b, v, G^T M p read,
-            # x_n, v, psi written; W_n
-            "update": 48.0 + 8.0 / s + 7 * NODE + (4.0 / 3.0) / s,
+            # every iteration: edges w, q read, w written; diag K, M_e; nodes v, G^T M p read, v,
+            # psi written; W_n.  Every other iteration also the correction of two iterations:
+            # edges x, a, a_prev read, x written; nodes x_n, b, b_prev read, x_n written
+            "update": 24.0 + 8.0 / s + 4 * NODE + (4.0 / 3.0) / s + (32.0 + 4 * NODE) / 2,
         },
     }
 
@@ -390,6 +391,46 @@ def run_sources(stream, n_src=4):
             "bitwise_equal_to_separate": bool(same)}
 
 
+def pass_roofline(tem, grid, model, shifts, stream, nside):
+    """Per-launch timing of the two FP32 passes with all shifts active (tem_profile_passes: CUDA
+    events on the launching stream, 20 iterations) and the roofline figures of both."""
+    prof = tem.profile_passes(grid, model.loop_xy, model.z_loop, shifts, tem.PREC_MIXED, n_iter=20, stream=stream)
+    peak, peak_kind = _peaks()
+    units = prof["units"]
+    s = len(shifts)
+    pb = pass_bytes(s)
+    tma = os.environ.get("TEM_FP32_STENCIL", "") != "pipe" and nside % 2 == 0
+
+    def gbs(nbytes, ms):
+        return nbytes * units / (ms * 1e-3) / 1e9
+
+    def leg(which, ms):
+        a = gbs(pb["survey"][which], ms)
+        k = gbs(pb["kernel"][which], ms)
+        return {"launch_ms": ms, "achieved": a, "frac": a / peak, "bytes_per_unit": pb["survey"][which],
+                "kernel_bytes": {"bytes_per_unit": pb["kernel"][which], "achieved": k, "frac": k / peak},
+                "traffic": _traffic(which, units)}
+
+    st = leg("stencil", prof["stencil_ms"])
+    up = leg("update", prof["update_ms"])
+    it_ms = prof["stencil_ms"] + prof["update_ms"]
+    it_survey = (pb["survey"]["stencil"] + pb["survey"]["update"])
+    it_kernel = (pb["kernel"]["stencil"] + pb["kernel"]["update"])
+    roofline = {"bound": "hbm", "kernel": "k_cocg_stencil_tma" if tma else "k_cocg_stencil_pipe",
+                "achieved": st["achieved"], "peak": peak, "unit": "GB/s", "frac": st["frac"],
+                "traffic": st["traffic"], "peak_source": peak_kind,
+                "bytes_per_unit": st["bytes_per_unit"], "units_per_launch": units,
+                "algorithmic_bytes_per_launch": st["bytes_per_unit"] * units, "launch_ms": st["launch_ms"],
+                "kernel_bytes": st["kernel_bytes"], "stencil_ctas_per_sm": prof["stencil_ctas_per_sm"],
+                "update": dict(up, kernel="k_cocg_update_vec" if tma else "k_cocg_update<float>"),
+                "iteration": {"ms": it_ms, "achieved": gbs(it_survey, it_ms), "frac": gbs(it_survey, it_ms) / peak,
+                              "kernel_bytes": {"achieved": gbs(it_kernel, it_ms), "frac": gbs(it_kernel, it_ms) / peak}},
+                "residual_ms": prof["residual_ms"],
+                "byte_counts": "achieved/frac: survey bytes (two-pass COCG vectors + M_e/s); kernel_bytes: what the "
+                               "kernels move incl. the nodal preconditioner (ncu-verified)"}
+    return roofline
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,6 +445,7 @@ def main():
     ap.add_argument("--serving-only", action="store_true")
     ap.add_argument("--no-derivatives", action="store_true")
     ap.add_argument("--no-single-time", action="store_true")
+    ap.add_argument("--passes-only", action="store_true", help="time the two FP32 passes only (no forward)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -435,6 +477,12 @@ def main():
     grid = tem.Grid(model.hx, model.hy, model.hz, model.origin, model.sigma, stream=stream)
     opt_mixed = tem.default_options(precision="mixed", tol=1e-12)
     opt_fp64 = tem.default_options(precision="fp64", tol=1e-12)
+    if args.passes_only:
+        # the pass timings alone (a short command to run under a profiler)
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "roofline": pass_roofline(tem, grid, model, shifts, stream,
+                                                                                 nside)}), flush=True)
+        return
 
     def fwd(opt, keep=False):
         return tem.forward(grid, model.loop_xy, model.z_loop, model.rx, shifts, c, opt, stream=stream,
@@ -513,40 +561,7 @@ def main():
     sources = run_sources(stream) if not args.no_single_time else None
 
     # per-launch timing of the passes with all shifts active (CUDA events on the launching stream)
-    prof = tem.profile_passes(grid, model.loop_xy, model.z_loop, shifts, tem.PREC_MIXED, n_iter=20, stream=stream)
-    peak, peak_kind = _peaks()
-    units = prof["units"]
-    s = len(shifts)
-    pb = pass_bytes(s)
-    tma = os.environ.get("TEM_FP32_STENCIL", "") != "pipe" and nside % 2 == 0
-
-    def gbs(nbytes, ms):
-        return nbytes * units / (ms * 1e-3) / 1e9
-
-    def leg(which, ms):
-        a = gbs(pb["survey"][which], ms)
-        k = gbs(pb["kernel"][which], ms)
-        return {"launch_ms": ms, "achieved": a, "frac": a / peak, "bytes_per_unit": pb["survey"][which],
-                "kernel_bytes": {"bytes_per_unit": pb["kernel"][which], "achieved": k, "frac": k / peak},
-                "traffic": _traffic(which, units)}
-
-    st = leg("stencil", prof["stencil_ms"])
-    up = leg("update", prof["update_ms"])
-    it_ms = prof["stencil_ms"] + prof["update_ms"]
-    it_survey = (pb["survey"]["stencil"] + pb["survey"]["update"])
-    it_kernel = (pb["kernel"]["stencil"] + pb["kernel"]["update"])
-    roofline = {"bound": "hbm", "kernel": "k_cocg_stencil_tma" if tma else "k_cocg_stencil_pipe",
-                "achieved": st["achieved"], "peak": peak, "unit": "GB/s", "frac": st["frac"],
-                "traffic": st["traffic"], "peak_source": peak_kind,
-                "bytes_per_unit": st["bytes_per_unit"], "units_per_launch": units,
-                "algorithmic_bytes_per_launch": st["bytes_per_unit"] * units, "launch_ms": st["launch_ms"],
-                "kernel_bytes": st["kernel_bytes"], "stencil_ctas_per_sm": prof["stencil_ctas_per_sm"],
-                "update": dict(up, kernel="k_cocg_update_vec" if tma else "k_cocg_update<float>"),
-                "iteration": {"ms": it_ms, "achieved": gbs(it_survey, it_ms), "frac": gbs(it_survey, it_ms) / peak,
-                              "kernel_bytes": {"achieved": gbs(it_kernel, it_ms), "frac": gbs(it_kernel, it_ms) / peak}},
-                "residual_ms": prof["residual_ms"],
-                "byte_counts": "achieved/frac: survey bytes (two-pass COCG vectors + M_e/s); kernel_bytes: what the "
-                               "kernels move incl. the nodal preconditioner (ncu-verified)"}
+    roofline = pass_roofline(tem, grid, model, shifts, stream, nside)
 
     # end to end through the C ABI from host buffers: grid upload + forward + result read-back
     e2e_steps = args.e2e_steps

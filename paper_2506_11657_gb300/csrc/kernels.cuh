@@ -938,6 +938,11 @@ static inline int stencil_pipe_occupancy() {
 // Convergence test and the next beta, from rho = (r, z) and rr = ||r||^2 (last CTA only).
 __device__ __forceinline__ void finish_iteration(SlotScalars* S, int* n_active, double rho_re, double rho_im,
                                                  double rr) {
+  // the update pass of this iteration (number S->iters) left alpha p out of d when it is even
+  S->lag = (S->iters & 1) == 0;
+  S->lag_par = S->parity;
+  S->alpha_prev_re = S->alpha_re;
+  S->alpha_prev_im = S->alpha_im;
   S->iters += 1;
   S->rr = rr;
   bool done = false;
@@ -996,7 +1001,11 @@ __device__ __forceinline__ void start_direction(SlotScalars* S, double rho_re, d
   S->rho_im = rho_im;
 }
 
-// ---------- pass B: x += alpha a, x_n += alpha b, r = D w - alpha q, w = r / D; (r, D^-1 r), ||r||
+// ---------- pass B: r = D w - alpha q, w = r / D; (r, D^-1 r), ||r||; v += alpha xi G^T M p,
+// psi = v / D_n; and, on odd iterations t, the correction of two iterations at once:
+//   x += alpha_{t-1} a_{t-1} + alpha_t a_t,  x_n += alpha_{t-1} b_{t-1} + alpha_t b_t
+// (both directions are still in the two direction buffers; x starts at 0 when t = 1).  An inner
+// solve that ends after an even t leaves alpha_t p_t to the residual pass (SlotScalars::lag).
 // A stream over the slot's entries [0, 3n) edges, [3n, 4n) nodes; boundary edges have
 // diag(K) = 0 and are left alone.
 template <class T>
@@ -1009,17 +1018,19 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
   const SlotDesc& d = A.slots[slot];
   const GridView& g = d.g;
   const C2<T> alpha(T(S->alpha_re), T(S->alpha_im));
+  const C2<T> alpha_prev(T(S->alpha_prev_re), T(S->alpha_prev_im));
   const C2<T> xi(T(d.xi_re), T(d.xi_im));
-  const bool first = S->iters == 0;                 // the correction starts at 0
+  const bool odd = (S->iters & 1) != 0;             // this pass adds two terms to the correction
+  const bool xzero = S->iters == 1;                 // ... which starts at 0
   const void* a = S->parity ? d.a0 : d.a1;          // the direction written by pass A
   const void* b = S->parity ? d.b0 : d.b1;
+  const void* ap = S->parity ? d.a1 : d.a0;         // the direction of the previous iteration
+  const void* bp = S->parity ? d.b1 : d.b0;
   typedef typename Vec2<T>::type V;
   const T* __restrict__ dK = Geo<T>(g).dK;
   const T* __restrict__ Me = Geo<T>(g).Me;
-  const V* __restrict__ av = static_cast<const V*>(a);
   const V* __restrict__ qv = static_cast<const V*>(d.q);
   V* __restrict__ wv = static_cast<V*>(d.w);
-  V* __restrict__ xv = static_cast<V*>(d.x);
   const int64_t ne = 3 * g.ncomp;
   const int64_t n = ne + (d.nodal ? g.ncomp : 0);
   const int64_t per = (n + d.nblk_update - 1) / d.nblk_update;
@@ -1031,18 +1042,15 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
   constexpr int U = 2;
   for (int64_t base = e0 + threadIdx.x; base < ee; base += (int64_t)NT * U) {
     T dk[U], me[U];
-    V ar[U], qr[U], wr[U], xr[U];
+    V qr[U], wr[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int64_t e = base + (int64_t)u * NT;
       if (e < ee) {
         dk[u] = __ldg(dK + e);
         me[u] = __ldg(Me + e);
-        ar[u] = __ldg(av + e);
         qr[u] = __ldg(qv + e);
         wr[u] = wv[e];
-        if (!first) xr[u] = xv[e];
-        else { xr[u].x = T(0); xr[u].y = T(0); }
       } else {
         dk[u] = T(0);
       }
@@ -1051,9 +1059,6 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
     for (int u = 0; u < U; ++u) {
       const int64_t e = base + (int64_t)u * NT;
       if (dk[u] == T(0)) continue;  // boundary entry (or past the range)
-      const C2<T> xn = C2<T>(xr[u].x, xr[u].y) + cmul(alpha, C2<T>(ar[u].x, ar[u].y));
-      V xo; xo.x = xn.re; xo.y = xn.im;
-      xv[e] = xo;
       const C2<T> D = C2<T>(dk[u], T(0)) - (me[u] * xi);
       const C2<T> r = cmul(D, C2<T>(wr[u].x, wr[u].y)) - cmul(alpha, C2<T>(qr[u].x, qr[u].y));
       const C2<T> wn = cdiv(r, D);
@@ -1063,15 +1068,12 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
       rr += r.re * r.re + r.im * r.im;
     }
   }
-  // nodal part: x_n += alpha b;  v = cn + xi G^T M d += alpha xi G^T M p;  psi = v / D_n
+  // nodal part: v = cn + xi G^T M d += alpha xi G^T M p;  psi = v / D_n
   // (v is kept in the u buffer: the start pass sets it to cn, so cn is not read here)
   const T* __restrict__ Wn = Geo<T>(g).Wn;
   C2<T> rn = czero<T>();
   for (int64_t e = max(e0, ne) + threadIdx.x; e < e1; e += NT) {
     const int64_t m = e - ne;
-    C2<T> xn = cmul(alpha, ld<T>(b, m));
-    if (!first) xn = xn + ld<T>(d.xn, m);
-    st<T>(d.xn, m, xn);
     const T wn = __ldg(Wn + m);
     if (wn == T(0)) continue;  // boundary node
     const C2<T> dv = ld<T>(d.u, m) + cmul(alpha, cmul(xi, ld<T>(d.gp, m)));
@@ -1079,6 +1081,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
     const C2<T> ps = cdiv(dv, wn * C2<T>(-xi.re, -xi.im));
     st<T>(d.psi, m, ps);
     rn = rn + cmul(dv, ps);
+  }
+  // the correction (odd iterations): boundary entries of both directions are 0, so x stays 0 there
+  if (odd) {
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += NT) {
+      const bool edge = e < ne;
+      const int64_t m = edge ? e : e - ne;
+      void* xd = edge ? d.x : d.xn;
+      C2<T> x = xzero ? czero<T>() : ld<T>(xd, m);
+      x = x + cmul(alpha_prev, ld<T>(edge ? ap : bp, m));
+      x = x + cmul(alpha, ld<T>(edge ? a : b, m));
+      st<T>(xd, m, x);
+    }
   }
   rz = rz + rn;
   double v[3] = {double(rz.re), double(rz.im), double(rr)};
@@ -1096,12 +1110,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 4 : 2) k_cocg_update(Batc
 // The arithmetic of k_cocg_update<float> on entry pairs (2e, 2e+1) of the slot's flat stream:
 // 3 n/2 edge pairs, then n/2 node pairs (n = nx ny nz, even for the slots that use this kernel).
 // Each thread keeps U pairs of every input in flight before it computes.
-__device__ __forceinline__ void update_edge(float& x_re, float& x_im, float& w_re, float& w_im, float a_re, float a_im,
-                                            float q_re, float q_im, float dk, float me, C2<float> alpha, float xr,
-                                            float xim, C2<float>& rz, float& rr) {
-  if (dk == 0.f) return;   // boundary entry: x and w stay as they are (0)
-  x_re += alpha.re * a_re - alpha.im * a_im;
-  x_im += alpha.re * a_im + alpha.im * a_re;
+__device__ __forceinline__ void update_edge(float& w_re, float& w_im, float q_re, float q_im, float dk, float me,
+                                            C2<float> alpha, float xr, float xim, C2<float>& rz, float& rr) {
+  if (dk == 0.f) return;   // boundary entry: w stays as it is (0)
   const C2<float> D(dk - me * xr, -me * xim);
   const C2<float> r = cmul(D, C2<float>(w_re, w_im)) - cmul(alpha, C2<float>(q_re, q_im));
   const C2<float> wn = cdiv(r, D);
@@ -1112,11 +1123,8 @@ __device__ __forceinline__ void update_edge(float& x_re, float& x_im, float& w_r
 }
 
 // v = cn + xi G^T M d (kept in the u buffer; the start pass sets it to cn): v += alpha xi G^T M p
-__device__ __forceinline__ void update_node(float& xn_re, float& xn_im, float& v_re, float& v_im, float& ps_re,
-                                            float& ps_im, float b_re, float b_im, float gp_re, float gp_im, float wn,
-                                            C2<float> alpha, C2<float> xi, C2<float>& rn) {
-  xn_re += alpha.re * b_re - alpha.im * b_im;
-  xn_im += alpha.re * b_im + alpha.im * b_re;
+__device__ __forceinline__ void update_node(float& v_re, float& v_im, float& ps_re, float& ps_im, float gp_re,
+                                            float gp_im, float wn, C2<float> alpha, C2<float> xi, C2<float>& rn) {
   if (wn == 0.f) return;   // boundary node: v and psi stay 0
   const C2<float> ag = cmul(alpha, cmul(xi, C2<float>(gp_re, gp_im)));
   v_re += ag.re;
@@ -1128,6 +1136,108 @@ __device__ __forceinline__ void update_node(float& xn_re, float& xn_im, float& v
   rn = rn + cmul(dv, ps);
 }
 
+// x + alpha_prev p_prev + alpha p on two complex entries
+__device__ __forceinline__ float4 add_two_terms(float4 x, float4 pp, float4 p, C2<float> alpha_prev, C2<float> alpha) {
+  x.x += alpha_prev.re * pp.x - alpha_prev.im * pp.y;
+  x.y += alpha_prev.re * pp.y + alpha_prev.im * pp.x;
+  x.z += alpha_prev.re * pp.z - alpha_prev.im * pp.w;
+  x.w += alpha_prev.re * pp.w + alpha_prev.im * pp.z;
+  x.x += alpha.re * p.x - alpha.im * p.y;
+  x.y += alpha.re * p.y + alpha.im * p.x;
+  x.z += alpha.re * p.z - alpha.im * p.w;
+  x.w += alpha.re * p.w + alpha.im * p.z;
+  return x;
+}
+
+// Pairs in flight per thread in pass B: odd iterations read three more arrays
+#ifndef TEM_UPD_U_ODD
+#define TEM_UPD_U_ODD 2
+#endif
+#ifndef TEM_UPD_U_EVEN
+#define TEM_UPD_U_EVEN 4
+#endif
+
+// Pointers and scalars of one slot's pass B on entry pairs.
+struct UpdVec {
+  C2<float> alpha, alpha_prev, xi;
+  bool xzero;
+  const float4 *a, *b, *ap, *bp, *q, *gp;
+  float4 *w, *x, *xn, *u, *psi;
+  const float2 *dK, *Me, *Wn;
+};
+
+// Edge pairs [from, to) with stride NT*U; ODD: also x += alpha_prev a_prev + alpha a.  Each
+// thread has U pairs of every input in flight before it computes (U larger when the pass reads
+// fewer arrays, so that about the same number of bytes are in flight).
+template <bool ODD, int U>
+__device__ __forceinline__ void update_edge_pairs(const UpdVec& P, int64_t from, int64_t to, C2<float>& rz, float& rr) {
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t base = from + threadIdx.x; base < to; base += (int64_t)NT * U) {
+    float2 dk[U], me[U];
+    float4 qr[U], wr[U], xr[U], ar[U], pr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + (int64_t)u * NT;
+      if (p < to) {
+        dk[u] = __ldg(P.dK + p);
+        me[u] = __ldg(P.Me + p);
+        qr[u] = __ldg(P.q + p);
+        wr[u] = P.w[p];
+        if (ODD) {
+          ar[u] = __ldg(P.a + p);
+          pr[u] = __ldg(P.ap + p);
+          xr[u] = P.xzero ? z4 : P.x[p];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t p = base + (int64_t)u * NT;
+      if (p >= to) continue;
+      update_edge(wr[u].x, wr[u].y, qr[u].x, qr[u].y, dk[u].x, me[u].x, P.alpha, P.xi.re, P.xi.im, rz, rr);
+      update_edge(wr[u].z, wr[u].w, qr[u].z, qr[u].w, dk[u].y, me[u].y, P.alpha, P.xi.re, P.xi.im, rz, rr);
+      P.w[p] = wr[u];
+      // boundary entries of both directions are 0, so x stays 0 there
+      if (ODD) P.x[p] = add_two_terms(xr[u], pr[u], ar[u], P.alpha_prev, P.alpha);
+    }
+  }
+}
+
+// Node pairs [from, to) (indices within the nodal vectors); ODD: also x_n += alpha_prev b_prev + alpha b.
+template <bool ODD, int U>
+__device__ __forceinline__ void update_node_pairs(const UpdVec& P, int64_t from, int64_t to, C2<float>& rn) {
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int64_t base = from + threadIdx.x; base < to; base += (int64_t)NT * U) {
+    float2 wn[U];
+    float4 gr[U], ur[U], xr[U], br[U], pr[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t m = base + (int64_t)u * NT;
+      if (m < to) {
+        wn[u] = __ldg(P.Wn + m);
+        gr[u] = __ldg(P.gp + m);
+        ur[u] = P.u[m];
+        if (ODD) {
+          br[u] = __ldg(P.b + m);
+          pr[u] = __ldg(P.bp + m);
+          xr[u] = P.xzero ? z4 : P.xn[m];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t m = base + (int64_t)u * NT;
+      if (m >= to) continue;
+      float4 ps = z4;
+      update_node(ur[u].x, ur[u].y, ps.x, ps.y, gr[u].x, gr[u].y, wn[u].x, P.alpha, P.xi, rn);
+      update_node(ur[u].z, ur[u].w, ps.z, ps.w, gr[u].z, gr[u].w, wn[u].y, P.alpha, P.xi, rn);
+      P.u[m] = ur[u];
+      P.psi[m] = ps;
+      if (ODD) P.xn[m] = add_two_terms(xr[u], pr[u], br[u], P.alpha_prev, P.alpha);
+    }
+  }
+}
+
 static __global__ void __launch_bounds__(NT, 3) k_cocg_update_vec(BatchArgs A) {
   __shared__ double red[NT / 32 * 4];
   const int2 bm = A.ublk2slot[blockIdx.x];
@@ -1136,85 +1246,40 @@ static __global__ void __launch_bounds__(NT, 3) k_cocg_update_vec(BatchArgs A) {
   if (!S->active) return;
   const SlotDesc& d = A.slots[slot];
   const int64_t nc = d.g.ncomp;
-  const C2<float> alpha(float(S->alpha_re), float(S->alpha_im));
-  const C2<float> xi(float(d.xi_re), float(d.xi_im));
-  const bool first = S->iters == 0;                 // the correction starts at 0
-  const float4* __restrict__ av = static_cast<const float4*>(S->parity ? d.a0 : d.a1);
-  const float4* __restrict__ bv = static_cast<const float4*>(S->parity ? d.b0 : d.b1);
-  const float4* __restrict__ qv = static_cast<const float4*>(d.q);
-  float4* __restrict__ wv = static_cast<float4*>(d.w);
-  float4* __restrict__ xv = static_cast<float4*>(d.x);
-  const float2* __restrict__ dK = reinterpret_cast<const float2*>(d.g.dKf);
-  const float2* __restrict__ Me = reinterpret_cast<const float2*>(d.g.Mef);
-  const float2* __restrict__ Wn = reinterpret_cast<const float2*>(d.g.Wnf);
+  UpdVec P;
+  P.alpha = C2<float>(float(S->alpha_re), float(S->alpha_im));
+  P.alpha_prev = C2<float>(float(S->alpha_prev_re), float(S->alpha_prev_im));
+  P.xi = C2<float>(float(d.xi_re), float(d.xi_im));
+  const bool odd = (S->iters & 1) != 0;             // this pass adds two terms to the correction
+  P.xzero = S->iters == 1;                          // ... which starts at 0
+  const int par = S->parity;                        // the direction written by pass A: a0/b0 if 1
+  P.a = static_cast<const float4*>(par ? d.a0 : d.a1);
+  P.b = static_cast<const float4*>(par ? d.b0 : d.b1);
+  P.ap = static_cast<const float4*>(par ? d.a1 : d.a0);
+  P.bp = static_cast<const float4*>(par ? d.b1 : d.b0);
+  P.q = static_cast<const float4*>(d.q);
+  P.gp = static_cast<const float4*>(d.gp);
+  P.w = static_cast<float4*>(d.w);
+  P.x = static_cast<float4*>(d.x);
+  P.xn = static_cast<float4*>(d.xn);
+  P.u = static_cast<float4*>(d.u);
+  P.psi = static_cast<float4*>(d.psi);
+  P.dK = reinterpret_cast<const float2*>(d.g.dKf);
+  P.Me = reinterpret_cast<const float2*>(d.g.Mef);
+  P.Wn = reinterpret_cast<const float2*>(d.g.Wnf);
   const int64_t ne2 = 3 * nc / 2, n2 = ne2 + (d.nodal ? nc / 2 : 0);
   const int64_t per = (n2 + d.nblk_update - 1) / d.nblk_update;
   const int64_t p0 = (int64_t)lb * per, p1 = min(n2, p0 + per);
   if (p1 > p0 && !TEM_CHECK(p1 - 1, n2, 12)) return;
   C2<float> rz = czero<float>(), rn = czero<float>();
   float rr = 0.f;
-  constexpr int U = 2;
-  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int64_t pe = min(p1, ne2);
-  for (int64_t base = p0 + threadIdx.x; base < pe; base += (int64_t)NT * U) {
-    float2 dk[U], me[U];
-    float4 ar[U], qr[U], wr[U], xr[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = base + (int64_t)u * NT;
-      if (p < pe) {
-        dk[u] = __ldg(dK + p);
-        me[u] = __ldg(Me + p);
-        ar[u] = __ldg(av + p);
-        qr[u] = __ldg(qv + p);
-        wr[u] = wv[p];
-        xr[u] = first ? z4 : xv[p];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t p = base + (int64_t)u * NT;
-      if (p >= pe) continue;
-      update_edge(xr[u].x, xr[u].y, wr[u].x, wr[u].y, ar[u].x, ar[u].y, qr[u].x, qr[u].y, dk[u].x, me[u].x, alpha,
-                  xi.re, xi.im, rz, rr);
-      update_edge(xr[u].z, xr[u].w, wr[u].z, wr[u].w, ar[u].z, ar[u].w, qr[u].z, qr[u].w, dk[u].y, me[u].y, alpha,
-                  xi.re, xi.im, rz, rr);
-      xv[p] = xr[u];
-      wv[p] = wr[u];
-    }
-  }
-  // nodal pairs: x_n += alpha b;  v = cn + xi G^T M d += alpha xi G^T M p;  psi = v / D_n
-  const float4* __restrict__ gpv = static_cast<const float4*>(d.gp);
-  float4* __restrict__ xnv = static_cast<float4*>(d.xn);
-  float4* __restrict__ uv = static_cast<float4*>(d.u);
-  float4* __restrict__ psv = static_cast<float4*>(d.psi);
-  for (int64_t base = max(p0, ne2) + threadIdx.x; base < p1; base += (int64_t)NT * U) {
-    float2 wn[U];
-    float4 br[U], gr[U], xr[U], ur[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t m = base + (int64_t)u * NT - ne2;
-      if (m + ne2 < p1) {
-        wn[u] = __ldg(Wn + m);
-        br[u] = __ldg(bv + m);
-        gr[u] = __ldg(gpv + m);
-        xr[u] = first ? z4 : xnv[m];
-        ur[u] = uv[m];
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t m = base + (int64_t)u * NT - ne2;
-      if (m + ne2 >= p1) continue;
-      float4 pr = z4;
-      update_node(xr[u].x, xr[u].y, ur[u].x, ur[u].y, pr.x, pr.y, br[u].x, br[u].y, gr[u].x, gr[u].y, wn[u].x,
-                  alpha, xi, rn);
-      update_node(xr[u].z, xr[u].w, ur[u].z, ur[u].w, pr.z, pr.w, br[u].z, br[u].w, gr[u].z, gr[u].w, wn[u].y,
-                  alpha, xi, rn);
-      xnv[m] = xr[u];
-      uv[m] = ur[u];
-      psv[m] = pr;
-    }
+  const int64_t pe = min(p1, ne2), m0 = max(p0, ne2) - ne2, m1 = p1 - ne2;
+  if (odd) {
+    update_edge_pairs<true, TEM_UPD_U_ODD>(P, p0, pe, rz, rr);
+    update_node_pairs<true, TEM_UPD_U_ODD>(P, m0, m1, rn);
+  } else {
+    update_edge_pairs<false, TEM_UPD_U_EVEN>(P, p0, pe, rz, rr);
+    update_node_pairs<false, TEM_UPD_U_EVEN>(P, m0, m1, rn);
   }
   rz = rz + rn;
   double v[3] = {double(rz.re), double(rz.im), double(rr)};
@@ -1352,6 +1417,8 @@ __global__ void __launch_bounds__(NT) k_cocg_nodal(BatchArgs A) {
 template <class TI>
 struct ResidualPol {
   const void* xcur; const void* de; const void* dn; void* xnext; double inv_sc; bool upd;
+  bool dok;                                   // de, dn hold the correction (else it starts at 0)
+  const void* pe; const void* pn; C2<double> alag;   // the term the update passes left out (pe NULL: none)
   const double* f; const void* rhs_c;
   C2<double> xi; const double* Me;
   Geo<TI> GI; Geo<double> G; const GridView* g; TI xr, xim;
@@ -1361,18 +1428,27 @@ struct ResidualPol {
   __device__ C2<double> load(int c, int i, int j, int k, int64_t idx, bool own) {
     C2<double> x = ld<double>(xcur, idx);
     if (upd && edge_valid(c, i, j, k)) {
-      const C2<TI> dv = ld<TI>(de, idx);
-      C2<double> corr(double(dv.re), double(dv.im));
-      if (dn) {
-        const int64_t n0 = i + (int64_t)g->nx * (j + (int64_t)g->ny * k);
-        const C2<TI> b0 = ld<TI>(dn, n0);
-        const C2<TI> gb = grad_edge<TI>(GI, *g, c, i, j, k, n0, b0, dn, czero<TI>(), nullptr, nullptr, false);
-        corr = corr + C2<double>(double(gb.re), double(gb.im));
-      }
+      const int64_t n0 = i + (int64_t)g->nx * (j + (int64_t)g->ny * k);
+      // d = d_e + G d_n, plus alag (p_e + G p_n) when the last update pass left that term out
+      C2<double> corr = czero<double>();
+      if (dok) corr = field_at(de, dn, c, i, j, k, idx, n0);
+      if (pe) corr = corr + cmul(alag, field_at(pe, pn, c, i, j, k, idx, n0));
       x = x + inv_sc * corr;
       if (own) st<double>(xnext, idx, x);
     }
     return x;
+  }
+  // (v_e + G v_n) on edge (c, i, j, k) in double, from an edge and a nodal vector of type TI
+  __device__ C2<double> field_at(const void* ve, const void* vn, int c, int i, int j, int k, int64_t idx,
+                                 int64_t n0) const {
+    const C2<TI> dv = ld<TI>(ve, idx);
+    C2<double> f(double(dv.re), double(dv.im));
+    if (vn) {
+      const C2<TI> b0 = ld<TI>(vn, n0);
+      const C2<TI> gb = grad_edge<TI>(GI, *g, c, i, j, k, n0, b0, vn, czero<TI>(), nullptr, nullptr, false);
+      f = f + C2<double>(double(gb.re), double(gb.im));
+    }
+    return f;
   }
   template <class U> __device__ void node(int64_t, int, int, int, U, U, U) {}
   __device__ void prefetch(int64_t, int, int, int) {}
@@ -1412,6 +1488,12 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
   pol.xnext = d.x64[S->xcur ^ 1];
   pol.de = d.x;
   pol.dn = d.nodal ? d.xn : nullptr;
+  // the update passes write the correction on odd iterations: it holds data once two
+  // iterations are done, and lacks the last term when the solve ended after an even one
+  pol.dok = S->iters >= 2;
+  pol.pe = S->lag ? (S->lag_par ? d.a0 : d.a1) : nullptr;
+  pol.pn = S->lag && d.nodal ? (S->lag_par ? d.b0 : d.b1) : nullptr;
+  pol.alag = C2<double>(S->alpha_prev_re, S->alpha_prev_im);
   pol.inv_sc = S->inv_scale_prev;
   pol.f = d.f;
   pol.rhs_c = d.rhs_c;
@@ -1457,6 +1539,7 @@ __global__ void __launch_bounds__(NT) k_residual(BatchArgs A, int* n_done) {
     const double rel2 = d.fp64_inner ? want : fmax(S->inner_rel2, want);
     S->tol2 = rel2 * S->bb;
     S->iters = 0;
+    S->lag = 0;
     S->rr_best = S->bb;
     S->it_best = 0;
     // continue the last inner solve's direction (residual replacement), or restart: first

@@ -202,6 +202,12 @@ struct SlotScalars {
   int32_t carry;            // keep the search direction across outer steps (residual replacement)
   int32_t stalled;          // the last inner solve ended on stagnation
   double carry_ratio;       // s_prev / s of an armed solve that continues the direction, else 0
+  // The update pass adds alpha p to the correction d on odd iterations only, two directions at
+  // a time (both are still in the direction buffers), so an inner solve that ends after an even
+  // iteration leaves its last term to the residual pass.
+  double alpha_prev_re, alpha_prev_im;   // alpha of the last completed iteration
+  int32_t lag;              // 1: d lacks alpha_prev p of the last completed iteration
+  int32_t lag_par;          // parity of that iteration (its direction is in a0/b0 if 1, else a1/b1)
 };
 
 }  // namespace tem
