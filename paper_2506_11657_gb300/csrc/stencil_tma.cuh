@@ -14,13 +14,14 @@
 // Positions outside the grid arrive as zeros (out-of-bounds fill), which is the value every
 // vector holds there.  a and b are formed in place in the landed stage; each thread then
 // computes the faces its three edges need straight from the formed planes (its own faces and
-// those at i-1 and j-1; the faces one plane below stay in registers), so one CTA barrier per
-// plane suffices: it separates forming plane k+1 from reading it, and it frees the stage that
-// the next TMA load overwrites.
+// those at i-1 and j-1; the faces one plane below stay in registers).  Two CTA barriers per
+// plane: one frees the stage that the next TMA load overwrites, the other separates forming
+// plane k+1 from reading it.
 //
 // Planes k0-1 .. k1 pass through the ring; plane p uses W/M stage (p - k0 + 1) mod NW and
-// a_old stage (p - k0 + 1) mod NO.  While plane k is computed, plane k+1 is formed and plane
-// k+2 is in flight.
+// a_old stage (p - k0 + 1) mod NO.  Each step k starts with a barrier (everyone is done with
+// plane k-1), issues plane k+2 into plane k-1's stage, then waits for plane k+1 and forms it:
+// two planes are in flight while a third is formed and computed.
 //
 // Every wait on an mbarrier is bounded (about one second of device time).  A CTA whose wait
 // runs out marks its slot TEM_ETIMEOUT and inactive, waits (again bounded) for the loads it
@@ -313,6 +314,18 @@ __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
 #pragma unroll 1
   for (int k = k0; k < k1 && !abort; ++k, qk += sxy, gk += sxy) {
     const int sk = (k - k0 + 1) % NW, sk1 = (k - k0 + 2) % NW;
+    // plane k+2 into the stage of plane k-1 before waiting for plane k+1, so that two planes are
+    // in flight: the barrier says that everyone has passed the last use of that stage (the
+    // arithmetic of plane k-1, or the column below at the chunk start).  Its a_old stage held
+    // plane k, formed before the previous barrier.
+    __syncthreads();
+    if (k + 2 <= k1) {
+      if (leader) {
+        fence_proxy_async();
+        issue_plane(R, maps, k + 2, (k + 3 - k0) % NW, (k + 3 - k0) % NO, i0, j0, nodal, use_beta, aold, bold);
+      }
+      issued = k - k0 + 4;
+    }
     // plane k+1 (count k-k0+2): landed -> formed
     ok = mbar_wait(R.bar(sk1), (unsigned)(((k - k0 + 2) / NW) & 1));
     if (ok) {
@@ -324,14 +337,6 @@ __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
     __syncthreads();
     abort = *R.flag() != 0;
     if (abort) break;
-    // plane k+2 into the stage of plane k-1 (free: everyone has passed its last use)
-    if (k + 2 <= k1) {
-      if (leader) {
-        fence_proxy_async();
-        issue_plane(R, maps, k + 2, (k + 3 - k0) % NW, (k + 3 - k0) % NO, i0, j0, nodal, use_beta, aold, bold);
-      }
-      issued = k - k0 + 4;
-    }
     if (!mine) continue;
     const float2* P = R.vec(sk);
     const float2* P1 = R.vec(sk1);
