@@ -271,14 +271,10 @@ __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
   if (ok) {
     waited = 1;
     form_plane(R, 0, 0, fp, sxy4 * (k0 - 1), false, nc4, nodal, use_beta, br, bi, anew, bnew);
-    ok = mbar_wait(R.bar(1), 0);
+  } else {
+    *R.flag() = 1;
   }
-  if (ok) {
-    waited = 2;
-    form_plane(R, 1, 1, fp, sxy4 * k0, true, nc4, nodal, use_beta, br, bi, anew, bnew);
-  }
-  if (!ok) *R.flag() = 1;
-  __syncthreads();
+  __syncthreads();   // plane k0-1 is formed: its a_old stage takes plane k0+1 while plane k0 lands
   bool abort = *R.flag() != 0;
   if (!abort && k0 + 1 <= k1) {
     if (leader) {
@@ -287,6 +283,17 @@ __global__ void __launch_bounds__(NT, 3) k_cocg_stencil_tma(BatchArgs A) {
     }
     issued = 3;
   }
+  if (!abort) {
+    ok = mbar_wait(R.bar(1), 0);
+    if (ok) {
+      waited = 2;
+      form_plane(R, 1, 1, fp, sxy4 * k0, true, nc4, nodal, use_beta, br, bi, anew, bnew);
+    } else {
+      *R.flag() = 1;
+    }
+  }
+  __syncthreads();
+  abort = *R.flag() != 0;
   // the column one plane below the chunk: F_x, F_y there, a_z, b, M_z and 1/Lz
   float2 fxm = make_float2(0.f, 0.f), fym = fxm, az_prev = fxm, b_prev = fxm;
   float mz_prev = 0.f, rz_prev = 0.f;
