@@ -37,6 +37,17 @@ size_t slot_vector_bytes(int64_t ncomp, int precision) {
   return 2 * v64 + 5 * ve + 7 * vn;
 }
 
+// Update-pass CTAs per slot: about TEM_UPD_PER_THREAD entries per thread, at most
+// TEM_UPD_MAX_BLOCKS CTAs (a function of the slot's grid only, like every decomposition here).
+// Each CTA first walks a chain of dependent loads (block list, slot scalars, descriptor) and ends
+// with a block reduction, so it should stream several rounds of pairs in between.
+#ifndef TEM_UPD_PER_THREAD
+#define TEM_UPD_PER_THREAD 32
+#endif
+#ifndef TEM_UPD_MAX_BLOCKS
+#define TEM_UPD_MAX_BLOCKS 512
+#endif
+
 SlotVectors carve_slot(void* base, int64_t ncomp, int precision) {
   const size_t es = precision == TEM_PREC_FP64 ? 16 : 8;
   const size_t v64 = align256(3 * (size_t)ncomp * 16);
@@ -63,7 +74,8 @@ void decompose_slot(SlotDesc& d, int nodal) {
   d.zchunks = (d.g.nz + d.zchunk - 1) / d.zchunk;
   d.nblk_stencil = d.tiles_x * d.tiles_y * d.zchunks;
   const int64_t n = 3 * d.g.ncomp + (nodal ? d.g.ncomp : 0);
-  d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (n + NT * 8 - 1) / (NT * 8)));
+  d.nblk_update = (int)std::max<int64_t>(1, std::min<int64_t>(TEM_UPD_MAX_BLOCKS, (n + NT * TEM_UPD_PER_THREAD - 1) /
+                                                                                    (NT * TEM_UPD_PER_THREAD)));
   d.nblk_nodal = (int)std::max<int64_t>(1, std::min<int64_t>(2048, (d.g.ncomp + NT * 8 - 1) / (NT * 8)));
 }
 
