@@ -157,3 +157,29 @@ def test_serving_stream_is_pinned():
     assert [m.degree for _, m in items] == [20, 18, 20, 19, 18, 20, 20, 17]
     assert np.allclose([a for a, _ in items], [3.798827, 4.229625, 7.469825, 7.611016, 8.551266, 9.34634,
                                                9.960733, 11.478622], atol=1e-6)
+
+
+def test_bench_byte_counts():
+    """The bytes per interior edge per shift that the bench divides by each pass's time, tallied
+    here array by array (complex FP32 = 8 B per entry; a nodal vector has one entry per three
+    edges; per-grid arrays are shared by the s shifts that sweep a tile together)."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    s = 10
+    node = 8.0 / 3.0
+    pb = bench.pass_bytes(s)
+    # two-pass COCG without a preconditioner's vectors: stencil r, p_old read, p, q written;
+    # update x, r, p, q read, x, r written; plus the M_e plane once per pass
+    assert pb["survey"]["stencil"] == pytest.approx(4 * 8 + 4.0 / s)
+    assert pb["survey"]["update"] == pytest.approx(6 * 8 + 4.0 / s)
+    # stencil: edges w, a_old, a, q; nodes psi, b_old, b, G^T M p; packed masses (16 B per node)
+    assert pb["kernel"]["stencil"] == pytest.approx(4 * 8 + 4 * node + 16.0 / 3.0 / s)
+    # update, even iterations: edges w (r/w), q; diag K and M_e (4 B each); nodes v (r/w), G^T M p,
+    # psi; W_n (4 B per node)
+    even = 3 * 8 + 8.0 / s + 4 * node + 4.0 / 3.0 / s
+    # odd iterations add the correction: edges x (r/w), a, a_prev; nodes x_n (r/w), b, b_prev
+    odd = even + 4 * 8 + 4 * node
+    assert pb["kernel"]["update"] == pytest.approx((even + odd) / 2)
+    assert (even, odd) == (pytest.approx(35.6, abs=0.05), pytest.approx(78.3, abs=0.05))
